@@ -1,0 +1,418 @@
+"""Benchmark of the fused modified-MRT LBM step on GB300.
+
+Workload (the headline configuration): D2Q9, 4096 x 4096 periodic, Gaussian
+hill, space- and time-varying velocity u = U0 (sin(2 pi y/L) cos(w t),
+sin(2 pi x/L) sin(w t)), U0 = 0.05, w = 2 pi / 2000, full anisotropic D of
+Eq. 44 at tau = 1, FP32 state. One bench step = one time step of the whole
+grid = one launch of the fused pull-stream + collide kernel.
+
+Prints ONE JSON line (rank 0). Multi-GPU runs are independent replicas (the
+path is one domain per GPU; there is no data-path collective).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 4096
+TAU = 1.0
+B_LU = {"f32": 80, "f16": 52, "bf16": 52}      # algorithmic DRAM bytes per lattice update
+WORKLOAD = "D2Q9 modified-MRT Gaussian hill, 4096x4096 periodic, time-varying vortex u, D of Eq. 44 (tau=1)"
+PROFILE = os.path.join(ROOT, "profiles", "step_d2q9_f32_vortex4096.md")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            j = json.load(fh)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1404_2363_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(store: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"source_sha\s*=\s*([0-9a-f]+)", txt)
+    m = re.search(rf"traffic_bytes_per_launch\[{store}\]\s*=\s*([0-9.eE+]+)", txt)
+    if not m or not m_hash or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, dev_index: int):
+        self.dev = dev_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self, window=None):
+        """Median SM clock and throttle reasons over the samples taken inside
+        ``window`` = (t0, t1) in time.time() seconds (all samples if None)."""
+        import datetime as _dt
+
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = _dt.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                clk = float(parts[1])
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            if window is not None and not (window[0] <= ts <= window[1]):
+                continue
+            sm.append(clk)
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_solver(store: str):
+    import torch
+
+    from paper_1404_2363_gb300 import workloads as W
+    from paper_1404_2363_gb300.solver import Solver
+
+    wl = W.vortex_workload(N_GRID, TAU)
+    s = Solver(nx=N_GRID, ny=N_GRID, storage=store)
+    s.set_D(wl["D"])
+    a = torch.from_numpy(wl["a"].astype(np.float32)).cuda()
+    sched = torch.from_numpy(W.vortex_schedule(2000).astype(np.float32)).cuda()
+    s.set_velocity(a, sched)
+    phi0 = torch.from_numpy(wl["phi0"].astype(np.float32)).cuda()
+    s.set_phi(phi0)
+    return s, wl, a, sched, phi0
+
+
+def time_steps(s, steps, warmup):
+    import torch
+
+    st = s.stream
+    s.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    s.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def parity_sample(O, store: str, nsteps: int = 24, half: int = 40, npts: int = 6):
+    """phi error of the full-size run against the FP64 oracle, on windows the
+    oracle computes one by one: a window of half-width `half` around each sample
+    point, run as its own periodic box, is exact on its central
+    (half - nsteps - 1)-wide patch because information moves one node per step."""
+    import torch
+
+    from paper_1404_2363_gb300 import workloads as W
+
+    s, wl, a, sched, phi0 = make_solver(store)
+    s.step(nsteps)
+    got = s.get_phi().cpu().numpy().astype(np.float64)
+    s.close()
+    a_np = wl["a"].astype(np.float32).astype(np.float64)
+    sc = W.vortex_schedule(2000).astype(np.float32).astype(np.float64)
+    p0 = wl["phi0"].astype(np.float32).astype(np.float64)
+    g = np.random.default_rng(11)
+    c0 = N_GRID // 2
+    pts = [(c0, c0), (c0 + 90, c0 - 60)] + [tuple(c0 + g.integers(-250, 250, 2)) for _ in range(npts - 2)]
+    n = 2 * half + 1
+    keep = half - nsteps - 1
+    num = den = 0.0
+    for (x0, y0) in pts:
+        ix = (np.arange(x0 - half, x0 + half + 1)) % N_GRID
+        iy = (np.arange(y0 - half, y0 + half + 1)) % N_GRID
+        win_phi = p0[np.ix_(iy, ix)]
+        win_a = a_np[:, iy][:, :, ix].reshape(2, -1)
+        p = O.Params(nx=n, ny=n, A=O.A_from_D(wl["D"]))
+        want = O.run(p, win_phi.reshape(-1), nsteps, u_of_t=lambda t: win_a * sc[t % len(sc)][:, None])
+        want = want.reshape(n, n)[half - keep:half + keep + 1, half - keep:half + keep + 1]
+        gw = got[np.ix_(iy, ix)][half - keep:half + keep + 1, half - keep:half + keep + 1]
+        num += float(((gw - want) ** 2).sum())
+        den += float((want ** 2).sum())
+    return float(np.sqrt(num / den)), f"{npts} windows of {2 * keep + 1}^2 cells after {nsteps} steps"
+
+
+def cpu_baseline(O, max_seconds: float = 20.0):
+    """The FP64 oracle, as it is, on the full 4096^2 workload for a bounded
+    number of steps on this host's cores."""
+    from paper_1404_2363_gb300 import workloads as W
+
+    wl = W.vortex_workload(N_GRID, TAU)
+    p = O.Params(nx=N_GRID, ny=N_GRID, A=O.A_from_D(wl["D"]))
+    a = wl["a"].astype(np.float32).astype(np.float64).reshape(2, -1)
+    sc = W.vortex_schedule(2000)
+    f = O.init_eq(p, wl["phi0"].astype(np.float32).astype(np.float64).reshape(-1), a * sc[0][:, None])
+    post = np.empty_like(f)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        f = O.step(p, f, a * sc[steps % len(sc)][:, None], post)
+        steps += 1
+        if time.perf_counter() - t0 > max_seconds * 0.5 or steps >= 8:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": N_GRID * N_GRID * steps / dt / 1e6, "unit": "MLUPS", "cores": O.max_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} full-grid steps of the 4096x4096 workload (FP64, {O.max_threads()} threads)"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle on the host cores, each step a bounded
+    sample of the workload (one time step of a 1024 x 256 strip of the grid)."""
+    if rank != 0:
+        return
+    import oracle as O
+
+    O.build()
+    from paper_1404_2363_gb300 import workloads as W
+
+    wl = W.vortex_workload(N_GRID, TAU)
+    nx, ny = 1024, 256
+    p = O.Params(nx=nx, ny=ny, A=O.A_from_D(wl["D"]))
+    a = wl["a"][:, :ny, :nx].astype(np.float32).astype(np.float64).reshape(2, -1)
+    sc = W.vortex_schedule(2000)
+    f = O.init_eq(p, wl["phi0"][:ny, :nx].astype(np.float32).astype(np.float64).reshape(-1), a * sc[0][:, None])
+    post = np.empty_like(f)
+    for k in range(args.warmup):
+        f = O.step(p, f, a * sc[k % len(sc)][:, None], post)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        f = O.step(p, f, a * sc[(args.warmup + k) % len(sc)][:, None], post)
+    dt = time.perf_counter() - t0
+    v = nx * ny * args.steps / dt / 1e6
+    sample = f"each step: one FP64 oracle time step of a {nx}x{ny} strip of the 4096^2 workload"
+    out = {"impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "storage": "f64"},
+           "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": O.max_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def e2e_run(store: str, steps: int):
+    """End to end through the C ABI with host buffers: H2D of the velocity field
+    and phi0 from pinned memory, K steps, D2H of phi."""
+    import torch
+
+    from paper_1404_2363_gb300 import workloads as W
+    from paper_1404_2363_gb300.solver import Solver
+
+    wl = W.vortex_workload(N_GRID, TAU)
+    s = Solver(nx=N_GRID, ny=N_GRID, storage=store)
+    s.set_D(wl["D"])
+    a_host = torch.from_numpy(wl["a"].astype(np.float32)).pin_memory()
+    sched_host = torch.from_numpy(W.vortex_schedule(2000).astype(np.float32)).pin_memory()
+    phi_host = torch.from_numpy(wl["phi0"].astype(np.float32)).pin_memory()
+    out_host = torch.empty_like(phi_host).pin_memory()
+    a_dev = torch.empty_like(a_host, device="cuda")
+    sched_dev = torch.empty_like(sched_host, device="cuda")
+    s.set_velocity(a_dev, sched_dev)
+    s.L.lbm_cde_run_host(s.h, phi_host.data_ptr(), 2, out_host.data_ptr())  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    a_dev.copy_(a_host, non_blocking=True)
+    sched_dev.copy_(sched_host, non_blocking=True)
+    st = s.L.lbm_cde_run_host(s.h, phi_host.data_ptr(), steps, out_host.data_ptr())
+    dt = time.perf_counter() - t0
+    s._ck(st, "lbm_cde_run_host")
+    s.close()
+    ncell = N_GRID * N_GRID
+    h2d = a_host.numel() * 4 + sched_host.numel() * 4 + ncell * 4
+    d2h = ncell * 4
+    return {"value": ncell * steps / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h / steps,
+            "note": f"one lbm_cde_run_host call of {steps} steps; per-step bytes are the call's copies / steps"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline and parity sample")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        barrier(world)
+        return
+
+    import paper_1404_2363_gb300 as P
+
+    P.lib()
+    store = "f32"
+    s, wl, a, sched, phi0 = make_solver(store)
+    ncell = N_GRID * N_GRID
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as cs:
+        time.sleep(0.5)                      # let the sampler start
+        t_wall0 = time.time()
+        dt = time_steps(s, args.steps, args.warmup)
+        t_wall1 = time.time()
+        time.sleep(0.25)
+    barrier(world)
+    dt_max = max_over_ranks(dt, world)
+    mass_ok = s.sum_phi()
+    s.close()
+    value = world * ncell * args.steps / dt_max / 1e6
+    avg_launch = dt / args.steps
+    peak, peak_kind = peaks()
+    achieved = ncell * B_LU[store] / avg_launch / 1e9
+
+    # reduced-precision storage forms of the same workload (same timing rules)
+    variants = {}
+    for vs in ("f16", "bf16"):
+        sv, *_ = make_solver(vs)
+        dtv = time_steps(sv, args.steps, args.warmup)
+        sv.close()
+        av = ncell * B_LU[vs] / (dtv / args.steps) / 1e9
+        variants[vs] = {"MLUPS": ncell * args.steps / dtv / 1e6, "bytes_per_lu": B_LU[vs],
+                        "achieved_gbs": av, "frac_of_" + peak_kind + "_hbm": av / peak}
+    torch.cuda.empty_cache()
+
+    e2e = e2e_run(store, args.steps)
+    if rank != 0:
+        barrier(world)
+        return
+
+    out = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt_max / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "storage": store, "tau": TAU,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2: 1.21 GB of state per step (129 MB L2)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profile_traffic(store),
+                     "peak_source": peak_kind, "bytes_per_lu": B_LU[store],
+                     "kernel": "k_step<D2Q9, F32, FIELD> (one launch per step)"},
+        "gpu_launches": args.steps,
+        "clocks": cs.summary((t_wall0, t_wall1)),
+        "variants": variants,
+        "e2e": e2e,
+        "sum_phi": mass_ok,
+    }
+    if not args.no_cpu:
+        import oracle as O
+
+        O.build()
+        err, sample = parity_sample(O, store)
+        out["parity"] = {"phi_rel_l2_vs_fp64": err, "sample": sample, "tolerance": 1e-5}
+        out["cpu_baseline"] = cpu_baseline(O)
+    print(json.dumps(out), flush=True)
+    barrier(world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * lbm_cde.h - C ABI of the GB300 (sm_103a) modified-MRT lattice Boltzmann
+ * solver for the convection-diffusion equation
+ *
+ *     d_t phi + div(phi u) = div(D grad phi)                          (Eq. 1)
+ *
+ * of Huang & Wu, "A modified multiple-relaxation-time lattice Boltzmann model
+ * for convection-diffusion equation" (arXiv:1404.2363).
+ *
+ * One time step (lbm_cde_step) is one fused CUDA kernel per cell:
+ *   pull-stream f_i(x) <- f'_i(x - e_i)                  (Eq. 5, pull form)
+ *   wall rules at the y = 0 / y = ny-1 nodes             (Sec. 3.2; see bc_*)
+ *   m = M f                                              (Eq. 11, 12 / A.2)
+ *   m' = m - S (m - m^eq(phi, u))  with the modified S   (Eq. 13, 30-31 / A.5)
+ *   f' = M^-1 m'                                         (Eq. 14)
+ * with m^eq of Eq. 15-16 (D2Q9) or Eq. A.3-A.4 (D3Q15).
+ *
+ * Conventions common to every entry point
+ *   - Lattice units: dx = dt = c = 1.
+ *   - Cell index c = x + nx * (y + ny * z); x (and z) are periodic, the two
+ *     y faces take bc_lo_y / bc_hi_y.
+ *   - "dev" pointers are CUDA device pointers on the current device; "host"
+ *     pointers are ordinary host memory (pinned memory is faster).
+ *   - Per-cell arrays of vectors are SoA: u[a * ncell + c], a = 0 .. dim-1.
+ *   - Every call is asynchronous on desc.stream unless documented as
+ *     synchronising; the caller keeps borrowed pointers valid until the work
+ *     that reads them has finished.
+ *   - No entry point throws, aborts or exits. Errors come back as lbm_status;
+ *     lbm_cde_last_error() gives a message. Faults detected on the device are
+ *     latched in a device status word and reported by the next synchronising
+ *     call (lbm_cde_sum_phi, lbm_cde_sync, lbm_cde_run_host).
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef LBM_CDE_H
+#define LBM_CDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_cde_s* lbm_cde_t;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_E_ARG = 1,         /* invalid argument (null pointer, bad size, bad enum) */
+    LBM_E_NOT_SPD = 2,     /* D not symmetric positive definite (Eq. 1)           */
+    LBM_E_STATE = 3,       /* call out of order (e.g. step before set_phi)         */
+    LBM_E_OOM = 4,         /* allocation failed                                    */
+    LBM_E_CUDA = 5,        /* a CUDA runtime call failed                           */
+    LBM_E_NONFINITE = 6,   /* phi became NaN/Inf (instability, tau -> 1/2, large u) */
+    LBM_E_TIMEOUT = 7,     /* a bounded device wait gave up                        */
+    LBM_E_UNSUPPORTED = 8  /* valid but not implemented combination                */
+} lbm_status;
+
+enum { LBM_D2Q9 = 9, LBM_D3Q15 = 15 };
+
+/* Wall kinds for the y faces. x (and z) are always periodic. */
+enum {
+    LBM_BC_PERIODIC = 0,    /* both y faces must then be periodic                   */
+    LBM_BC_NOFLUX_NODE = 1, /* wall on the boundary node, Neumann d phi/dy = 0 by the
+                               mirror rule of Sec. 3.2: at y = 0 f2=f4, f5=f8,
+                               f6=f7; at y = ny-1 f4=f2, f7=f6, f8=f5 (D3Q15: every
+                               population entering from beyond the wall copies its
+                               mirror image in y)                                   */
+    LBM_BC_BOUNCEBACK = 2,  /* halfway bounce-back: a population leaving through the
+                               wall returns to its node reversed (conserves sum phi) */
+    LBM_BC_DIRICHLET = 3    /* wall on the node, phi = phi_w: every population
+                               entering from beyond the wall is f^eq_i(phi*, u) with
+                               phi* chosen so that sum_i f_i = phi_w (not in the
+                               paper)                                               */
+};
+
+/* Storage form of the distributions between steps. Collision arithmetic is
+ * FP32 in every form. */
+enum {
+    LBM_STORE_F32 = 0,      /* f'_i in FP32                                          */
+    LBM_STORE_F16_NEQ = 1,  /* g_i = f'_i - f^eq_i(phi, u) in FP16, phi in FP32     */
+    LBM_STORE_BF16_NEQ = 2  /* g_i in BF16, phi in FP32                              */
+};
+
+/* Velocity representations (lbm_cde_set_velocity). */
+enum {
+    LBM_U_NONE = 0,         /* u = 0                                                 */
+    LBM_U_FIELD = 1,        /* u(x, t) = a(x) * s(t), a: [dim][ncell]                */
+    LBM_U_ROW_PROFILE = 2   /* u(x, t) = a(y) * s(t), a: [dim][ny]                   */
+};
+
+typedef struct {
+    int32_t lattice;         /* LBM_D2Q9 or LBM_D3Q15                                */
+    int32_t storage;         /* LBM_STORE_*                                          */
+    int64_t nx, ny, nz;      /* nz = 1 for D2Q9; nx >= 2, ny >= 3 (walls) or >= 1    */
+    int32_t bc_lo_y;         /* LBM_BC_* on the y = 0 face                           */
+    int32_t bc_hi_y;         /* LBM_BC_* on the y = ny-1 face                        */
+    double phi_w_lo_y;       /* Dirichlet value on y = 0                             */
+    double phi_w_hi_y;       /* Dirichlet value on y = ny-1                          */
+    double alpha1, alpha2;   /* free equilibrium parameters (Eq. 15b-c / A.3b-c);
+                                NaN selects the defaults: D2Q9 -8, 8 (Eq. 37);
+                                D3Q15 -6/5, 192 (A.6 factor 1/3)                     */
+    double s[15];            /* diagonal relaxation rates s_0 .. s_{q-1}; NaN selects
+                                the defaults s1 = s2 = 1.1, s7.. = 1.2, s4 = s6 (= s8)
+                                = 1 (Sec. 3.1). Entries of the flux rows (3, 5, 7)
+                                are ignored: they come from lbm_cde_set_D.           */
+    int32_t tie_q_rates;     /* 1: s4 = sxx, s6 = syy (, s8 = szz) as in Sec. 3.1    */
+    /* Optional device allocator (e.g. the caller's caching allocator). When alloc
+       is NULL the library calls cudaMalloc / cudaFree. */
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free_)(void* ptr, void* ctx);
+    void* alloc_ctx;
+    void* stream;            /* cudaStream_t for every launch (NULL: legacy stream)  */
+} lbm_cde_desc;
+
+/* Fills *d with defaults for a periodic grid (F32 storage, default alpha and
+ * rates, tie_q_rates = 1, no allocator, NULL stream). */
+lbm_status lbm_cde_desc_init(lbm_cde_desc* d, int32_t lattice, int64_t nx, int64_t ny, int64_t nz);
+
+/* Creates a solver. Allocates two state buffers (ping-pong) plus small scratch
+ * through desc->alloc. The handle owns that memory until lbm_cde_destroy.
+ * Errors: LBM_E_ARG (bad desc), LBM_E_OOM, LBM_E_CUDA. */
+lbm_status lbm_cde_create(const lbm_cde_desc* desc, lbm_cde_t* out);
+
+/* Synchronises the stream, frees everything the handle owns. NULL is a no-op. */
+lbm_status lbm_cde_destroy(lbm_cde_t h);
+
+/* Sets the diffusion tensor. D is dim x dim, row-major, host memory, lattice
+ * units. The relaxation block is A = (D / k + I / 2)^-1 with
+ * k = 2/3 + alpha1/8 + alpha2/12 (Eq. 36) or 2/3 + 55 alpha1/54 + alpha2/216
+ * (Eq. A.6); A enters S through Eq. 30-31 / A.5.
+ * Errors: LBM_E_ARG (NULL), LBM_E_NOT_SPD (D not symmetric to 1e-12 relative or
+ * not positive definite, or k <= 0). */
+lbm_status lbm_cde_set_D(lbm_cde_t h, const double* D);
+
+/* Reads back the relaxation block A (dim x dim, host) and the 15 diagonal rates
+ * in use (host, may be NULL). */
+lbm_status lbm_cde_get_rates(lbm_cde_t h, double* A_out, double* s_out);
+
+/* Sets the velocity u(x, t) = a(x) * s(t) used by the collision at step t
+ * (t = 0 for the initial equilibrium).
+ *   kind     : LBM_U_NONE / LBM_U_FIELD / LBM_U_ROW_PROFILE
+ *   a_dev    : device FP32, [dim][ncell] (FIELD) or [dim][ny] (ROW_PROFILE);
+ *              borrowed until the next set_velocity or destroy
+ *   sched_dev: device FP32 [sched_len][dim] per-component multipliers s(t),
+ *              indexed by t mod sched_len; NULL means s = 1
+ * Errors: LBM_E_ARG. */
+lbm_status lbm_cde_set_velocity(lbm_cde_t h, int32_t kind, const float* a_dev,
+                                const float* sched_dev, int64_t sched_len);
+
+/* Initialises f = f^eq(phi, u(x, 0)) from a device FP32 field phi_dev [ncell]
+ * and resets the step counter to 0. */
+lbm_status lbm_cde_set_phi(lbm_cde_t h, const float* phi_dev);
+
+/* Advances nsteps time steps (asynchronous; one kernel launch per step). */
+lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps);
+
+/* Sets the launch shape of the step kernel: block threads per CTA along x
+ * (a multiple of 32 in [32, 1024]) and vec cells per thread (1 or 2). Results
+ * do not depend on the shape. Errors: LBM_E_ARG. */
+lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec);
+
+/* Number of steps taken since the last set_phi / set_state. */
+lbm_status lbm_cde_get_time(lbm_cde_t h, int64_t* t_out);
+
+/* Writes phi = sum_i f_i (Eq. 8) of the current state into phi_dev [ncell]
+ * (device FP32, caller-owned). Asynchronous. */
+lbm_status lbm_cde_get_phi(lbm_cde_t h, float* phi_dev);
+
+/* Deterministic FP64 sum of phi over all cells (fixed two-pass order).
+ * Synchronises the stream; returns LBM_E_NONFINITE if the sum is not finite and
+ * any latched device status. */
+lbm_status lbm_cde_sum_phi(lbm_cde_t h, double* out_host);
+
+/* Synchronises the stream and returns the latched device status. */
+lbm_status lbm_cde_sync(lbm_cde_t h);
+
+/* Size in bytes of the raw state (for checkpoints). */
+lbm_status lbm_cde_state_bytes(lbm_cde_t h, size_t* bytes_out);
+
+/* Copies the raw state to / from a caller buffer (device or host memory,
+ * cudaMemcpyDefault) together with the step counter. Resuming from a saved
+ * state reproduces the uninterrupted run bit for bit. */
+lbm_status lbm_cde_get_state(lbm_cde_t h, void* dst, int64_t* t_out);
+lbm_status lbm_cde_set_state(lbm_cde_t h, const void* src, int64_t t);
+
+/* End-to-end convenience call with host buffers: copies phi0_host [ncell] to
+ * the device, initialises, runs nsteps, and copies phi back to phi_out_host
+ * [ncell]. Synchronising. */
+lbm_status lbm_cde_run_host(lbm_cde_t h, const float* phi0_host, int64_t nsteps, float* phi_out_host);
+
+/* Message for the last error on this handle (static storage owned by the
+ * handle; NULL handle gives the last creation error). */
+const char* lbm_cde_last_error(lbm_cde_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_CDE_H */

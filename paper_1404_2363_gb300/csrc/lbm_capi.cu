@@ -1,0 +1,505 @@
+// Host runtime behind the C ABI of include/lbm_cde.h: handle, buffers,
+// parameter derivation (D -> A, Eq. 36 / A.6), ping-pong stepping, reductions,
+// checkpoints. Every entry point catches its own failures and returns a status.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lbm_cde.h"
+#include "lbm_internal.cuh"
+
+using lbm::LaunchCfg;
+using lbm::StepArgs;
+
+struct lbm_cde_s {
+    lbm_cde_desc d{};
+    int q = 9, dim = 2;
+    long long ncell = 0;
+    size_t elem = 4;
+    bool neq = false;
+    void* state[2] = {nullptr, nullptr};
+    float* phi[2] = {nullptr, nullptr};
+    float* phi_tmp = nullptr;      // host round trips (run_host)
+    double* partials = nullptr;    // reduction scratch
+    double* sum_dev = nullptr;
+    int nparts = 0;
+    int cur = 0;
+    lbm::Coef coef{};
+    double A[9] = {0};
+    double s[15] = {0};
+    double alpha1 = 0, alpha2 = 0;
+    bool d_set = false;
+    int ukind = LBM_U_NONE;
+    const float* ua = nullptr;
+    const float* sched = nullptr;
+    long long sched_len = 0;
+    long long t = 0;
+    bool ready = false;
+    LaunchCfg cfg{256, 1};
+    cudaStream_t st = nullptr;
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+static lbm_status fail(lbm_cde_t h, lbm_status s, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else g_create_err = msg;
+    return s;
+}
+
+static lbm_status cuda_fail(lbm_cde_t h, cudaError_t e, const char* what)
+{
+    return fail(h, LBM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                         \
+    do {                                                    \
+        cudaError_t _e = (call);                            \
+        if (_e != cudaSuccess) return cuda_fail(h, _e, #call); \
+    } while (0)
+
+static void* dev_alloc(lbm_cde_t h, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (h->d.alloc) return h->d.alloc(bytes, h->d.alloc_ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void dev_free(lbm_cde_t h, void* p)
+{
+    if (!p) return;
+    if (h->d.free_) h->d.free_(p, h->d.alloc_ctx);
+    else if (!h->d.alloc) cudaFree(p);
+}
+
+// ---------------------------------------------------------------------------
+// Parameters
+// ---------------------------------------------------------------------------
+static double diffusion_factor(int q, double a1, double a2)
+{
+    if (q == 9) return 2.0 / 3.0 + a1 / 8.0 + a2 / 12.0;          // Eq. 36
+    return 2.0 / 3.0 + 55.0 / 54.0 * a1 + a2 / 216.0;             // Eq. A.6
+}
+
+// Inverse of a small dense matrix (n <= 3) by cofactors; returns false if singular.
+static bool small_inverse(int n, const double* a, double* inv)
+{
+    if (n == 2) {
+        const double det = a[0] * a[3] - a[1] * a[2];
+        if (det == 0.0 || !std::isfinite(det)) return false;
+        inv[0] = a[3] / det; inv[1] = -a[1] / det;
+        inv[2] = -a[2] / det; inv[3] = a[0] / det;
+        return true;
+    }
+    const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8],
+                 c02 = a[3] * a[7] - a[4] * a[6];
+    const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    if (det == 0.0 || !std::isfinite(det)) return false;
+    inv[0] = c00 / det;
+    inv[1] = (a[2] * a[7] - a[1] * a[8]) / det;
+    inv[2] = (a[1] * a[5] - a[2] * a[4]) / det;
+    inv[3] = c01 / det;
+    inv[4] = (a[0] * a[8] - a[2] * a[6]) / det;
+    inv[5] = (a[2] * a[3] - a[0] * a[5]) / det;
+    inv[6] = c02 / det;
+    inv[7] = (a[1] * a[6] - a[0] * a[7]) / det;
+    inv[8] = (a[0] * a[4] - a[1] * a[3]) / det;
+    return true;
+}
+
+// Positive definiteness of a symmetric matrix by Cholesky.
+static bool spd(int n, const double* a)
+{
+    double L[9] = {0};
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = a[i * n + j];
+            for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[i * n + i] = std::sqrt(s);
+            } else {
+                L[i * n + j] = s / L[j * n + j];
+            }
+        }
+    return true;
+}
+
+static void refresh_coef(lbm_cde_t h)
+{
+    lbm::Coef& c = h->coef;
+    const int n = h->dim;
+    double s[15];
+    for (int k = 0; k < 15; ++k) s[k] = h->s[k];
+    if (h->d.tie_q_rates) {
+        s[4] = h->A[0];
+        s[6] = h->A[n + 1];
+        if (n == 3) s[8] = h->A[8];
+    }
+    for (int k = 0; k < 15; ++k) c.s[k] = (float)s[k];
+    for (int k = 0; k < 9; ++k) c.A[k] = 0.f, c.C[k] = 0.f;
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+            const double Aab = h->A[a * n + b];
+            c.A[a * n + b] = (float)Aab;
+            // Eq. 30a-b / A.5: coupling of flux row a to q-moment b
+            c.C[a * n + b] = (float)((Aab / 2.0 - (a == b ? 1.0 : 0.0)) * s[4 + 2 * b]);
+        }
+    const double a1 = h->alpha1, a2 = h->alpha2;
+    if (h->q == 9) {
+        c.meq1 = (float)(a1 / 4.0);
+        c.meq2 = (float)(a2 / 4.0);
+        // Eq. 17
+        c.w0 = (float)((-a1 + a2 + 4.0) / 36.0);
+        c.wa = (float)((-a1 - 2.0 * a2 + 16.0) / 144.0);
+        c.wd = (float)((2.0 * a1 + a2 + 16.0) / 144.0);
+        c.ka = (float)(48.0 / 144.0);
+        c.kd = (float)(12.0 / 144.0);
+    } else {
+        c.meq1 = (float)(5.0 * a1 / 6.0);
+        c.meq2 = (float)(a2 / 24.0);
+        // f^eq = M^-1 m^eq for Eq. A.3 with c1 = 1, c2 = -4 (Eq. A.4)
+        c.w0 = (float)(1.0 / 15.0 - 5.0 * a1 / 54.0 + a2 / 540.0);
+        c.wa = (float)(1.0 / 15.0 - 5.0 * a1 / 108.0 - a2 / 2160.0);
+        c.wd = (float)(1.0 / 15.0 + 5.0 * a1 / 108.0 + a2 / 8640.0);
+        c.ka = (float)(1.0 / 5.0);
+        c.kd = (float)(3.0 / 40.0);
+    }
+}
+
+static StepArgs make_args(lbm_cde_t h, int src_idx)
+{
+    StepArgs a{};
+    a.src = h->state[src_idx];
+    a.dst = h->state[1 - src_idx];
+    a.phi_src = h->phi[src_idx];
+    a.phi_dst = h->phi[1 - src_idx];
+    a.ua = h->ua;
+    a.sched = h->sched;
+    a.sched_len = h->sched_len;
+    a.k = h->t + 1;
+    a.nx = (int)h->d.nx;
+    a.ny = (int)h->d.ny;
+    a.nz = (int)h->d.nz;
+    a.ncell = h->ncell;
+    a.bc_lo = h->d.bc_lo_y;
+    a.bc_hi = h->d.bc_hi_y;
+    a.phiw_lo = (float)h->d.phi_w_lo_y;
+    a.phiw_hi = (float)h->d.phi_w_hi_y;
+    a.c = h->coef;
+    return a;
+}
+
+static int ukind_internal(int k)
+{
+    return k == LBM_U_FIELD ? lbm::U_FIELD : (k == LBM_U_ROW_PROFILE ? lbm::U_ROW : lbm::U_NONE);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+lbm_status lbm_cde_desc_init(lbm_cde_desc* d, int32_t lattice, int64_t nx, int64_t ny, int64_t nz)
+{
+    if (!d) return fail(nullptr, LBM_E_ARG, "desc is NULL");
+    std::memset(d, 0, sizeof(*d));
+    d->lattice = lattice;
+    d->storage = LBM_STORE_F32;
+    d->nx = nx;
+    d->ny = ny;
+    d->nz = nz;
+    d->bc_lo_y = d->bc_hi_y = LBM_BC_PERIODIC;
+    d->alpha1 = d->alpha2 = NAN;
+    for (int k = 0; k < 15; ++k) d->s[k] = NAN;
+    d->tie_q_rates = 1;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_create(const lbm_cde_desc* desc, lbm_cde_t* out)
+{
+    if (!desc || !out) return fail(nullptr, LBM_E_ARG, "desc/out is NULL");
+    *out = nullptr;
+    const lbm_cde_desc& d = *desc;
+    if (d.lattice != LBM_D2Q9 && d.lattice != LBM_D3Q15)
+        return fail(nullptr, LBM_E_ARG, "lattice must be LBM_D2Q9 or LBM_D3Q15");
+    if (d.storage < LBM_STORE_F32 || d.storage > LBM_STORE_BF16_NEQ)
+        return fail(nullptr, LBM_E_ARG, "bad storage");
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1 || (d.lattice == LBM_D2Q9 && d.nz != 1))
+        return fail(nullptr, LBM_E_ARG, "bad grid size (D2Q9 needs nz = 1)");
+    if (d.nx > (1LL << 30) || d.ny > 65535 || d.nz > 65535)
+        return fail(nullptr, LBM_E_ARG, "grid too large (nx <= 2^30, ny, nz <= 65535)");
+    const long long ncell = d.nx * d.ny * d.nz;
+    if (ncell > (1LL << 40)) return fail(nullptr, LBM_E_ARG, "grid too large");
+    for (int side = 0; side < 2; ++side) {
+        const int b = side ? d.bc_hi_y : d.bc_lo_y;
+        if (b < LBM_BC_PERIODIC || b > LBM_BC_DIRICHLET) return fail(nullptr, LBM_E_ARG, "bad bc");
+    }
+    if ((d.bc_lo_y == LBM_BC_PERIODIC) != (d.bc_hi_y == LBM_BC_PERIODIC))
+        return fail(nullptr, LBM_E_ARG, "periodic y needs both y faces periodic");
+    if (d.bc_lo_y != LBM_BC_PERIODIC && d.ny < 3)
+        return fail(nullptr, LBM_E_ARG, "walls need ny >= 3");
+    if ((d.alloc == nullptr) != (d.free_ == nullptr))
+        return fail(nullptr, LBM_E_ARG, "alloc and free_ must both be set or both NULL");
+
+    lbm_cde_t h = new (std::nothrow) lbm_cde_s();
+    if (!h) return fail(nullptr, LBM_E_OOM, "host allocation failed");
+    h->d = d;
+    h->q = d.lattice;
+    h->dim = d.lattice == LBM_D2Q9 ? 2 : 3;
+    h->ncell = ncell;
+    h->neq = d.storage != LBM_STORE_F32;
+    h->elem = h->neq ? 2 : 4;
+    h->st = static_cast<cudaStream_t>(d.stream);
+    h->alpha1 = std::isnan(d.alpha1) ? (h->q == 9 ? -8.0 : -6.0 / 5.0) : d.alpha1;
+    h->alpha2 = std::isnan(d.alpha2) ? (h->q == 9 ? 8.0 : 192.0) : d.alpha2;
+    const double defaults9[15] = {1.0, 1.1, 1.1, 0, 1.0, 0, 1.0, 1.2, 1.2, 0, 0, 0, 0, 0, 0};
+    const double defaults15[15] = {1.0, 1.1, 1.1, 0, 1.0, 0, 1.0, 0, 1.0, 1.2, 1.2, 1.2, 1.2, 1.2, 1.2};
+    for (int k = 0; k < 15; ++k)
+        h->s[k] = std::isnan(d.s[k]) ? (h->q == 9 ? defaults9[k] : defaults15[k]) : d.s[k];
+    if (diffusion_factor(h->q, h->alpha1, h->alpha2) <= 0.0) {
+        delete h;
+        return fail(nullptr, LBM_E_ARG, "alpha1/alpha2 give a non-positive diffusion factor (Eq. 36 / A.6)");
+    }
+    for (int a = 0; a < h->dim; ++a) h->A[a * h->dim + a] = 1.0;  // replaced by set_D
+    refresh_coef(h);
+
+    const size_t plane_bytes = (size_t)ncell * h->elem;
+    for (int b = 0; b < 2; ++b) {
+        h->state[b] = dev_alloc(h, plane_bytes * h->q);
+        if (!h->state[b]) {
+            lbm_cde_destroy(h);
+            return fail(nullptr, LBM_E_OOM, "state allocation failed");
+        }
+        if (h->neq) {
+            h->phi[b] = static_cast<float*>(dev_alloc(h, (size_t)ncell * 4));
+            if (!h->phi[b]) {
+                lbm_cde_destroy(h);
+                return fail(nullptr, LBM_E_OOM, "phi allocation failed");
+            }
+        }
+    }
+    long long nb = (ncell + 255) / 256;
+    h->nparts = (int)(nb < 152 * 8 ? nb : 152 * 8);
+    if (h->nparts < 1) h->nparts = 1;
+    h->partials = static_cast<double*>(dev_alloc(h, sizeof(double) * (h->nparts + 1)));
+    if (!h->partials) {
+        lbm_cde_destroy(h);
+        return fail(nullptr, LBM_E_OOM, "scratch allocation failed");
+    }
+    h->sum_dev = h->partials + h->nparts;
+    // launch shape: 256 threads along x, cells per thread chosen for the row length
+    h->cfg.block = d.nx >= 256 ? 256 : (d.nx >= 128 ? 128 : 64);
+    h->cfg.vec = 1;
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_destroy(lbm_cde_t h)
+{
+    if (!h) return LBM_OK;
+    cudaStreamSynchronize(h->st);
+    for (int b = 0; b < 2; ++b) {
+        dev_free(h, h->state[b]);
+        dev_free(h, h->phi[b]);
+    }
+    dev_free(h, h->phi_tmp);
+    dev_free(h, h->partials);
+    delete h;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_set_D(lbm_cde_t h, const double* D)
+{
+    if (!h || !D) return fail(h, LBM_E_ARG, "NULL argument");
+    const int n = h->dim;
+    double scale = 0.0;
+    for (int k = 0; k < n * n; ++k) {
+        if (!std::isfinite(D[k])) return fail(h, LBM_E_NOT_SPD, "D has a non-finite entry");
+        scale = std::fmax(scale, std::fabs(D[k]));
+    }
+    for (int a = 0; a < n; ++a)
+        for (int b = a + 1; b < n; ++b)
+            if (std::fabs(D[a * n + b] - D[b * n + a]) > 1e-12 * scale)
+                return fail(h, LBM_E_NOT_SPD, "D is not symmetric");
+    if (!spd(n, D)) return fail(h, LBM_E_NOT_SPD, "D is not positive definite");
+    const double k = diffusion_factor(h->q, h->alpha1, h->alpha2);
+    double Ainv[9], A[9];
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) Ainv[a * n + b] = D[a * n + b] / k + (a == b ? 0.5 : 0.0);
+    if (!small_inverse(n, Ainv, A)) return fail(h, LBM_E_NOT_SPD, "A^-1 = D/k + I/2 is singular");
+    for (int a = 0; a < n * n; ++a) h->A[a] = A[a];
+    h->d_set = true;
+    refresh_coef(h);
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_get_rates(lbm_cde_t h, double* A_out, double* s_out)
+{
+    if (!h || !A_out) return fail(h, LBM_E_ARG, "NULL argument");
+    for (int a = 0; a < h->dim * h->dim; ++a) A_out[a] = h->A[a];
+    if (s_out)
+        for (int k = 0; k < 15; ++k) s_out[k] = h->coef.s[k];
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_set_velocity(lbm_cde_t h, int32_t kind, const float* a_dev, const float* sched_dev,
+                                int64_t sched_len)
+{
+    if (!h) return fail(h, LBM_E_ARG, "NULL handle");
+    if (kind != LBM_U_NONE && kind != LBM_U_FIELD && kind != LBM_U_ROW_PROFILE)
+        return fail(h, LBM_E_ARG, "bad velocity kind");
+    if (kind != LBM_U_NONE && !a_dev) return fail(h, LBM_E_ARG, "velocity pointer is NULL");
+    if (sched_dev && sched_len <= 0) return fail(h, LBM_E_ARG, "sched_len must be > 0");
+    h->ukind = kind;
+    h->ua = kind == LBM_U_NONE ? nullptr : a_dev;
+    h->sched = sched_dev;
+    h->sched_len = sched_dev ? sched_len : 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_set_phi(lbm_cde_t h, const float* phi_dev)
+{
+    if (!h || !phi_dev) return fail(h, LBM_E_ARG, "NULL argument");
+    if (!h->d_set) return fail(h, LBM_E_STATE, "set_D must come before set_phi");
+    h->cur = 0;
+    h->t = 0;
+    StepArgs a = make_args(h, 1);  // dst = state[0]
+    a.dst = h->state[0];
+    a.phi_dst = h->phi[0];
+    CK(h, lbm::launch_init(h->q, h->d.storage, ukind_internal(h->ukind), phi_dev, a, h->st));
+    h->ready = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps)
+{
+    if (!h || nsteps < 0) return fail(h, LBM_E_ARG, "bad argument");
+    if (!h->ready) return fail(h, LBM_E_STATE, "set_phi must come before step");
+    const bool walls = h->d.bc_lo_y != LBM_BC_PERIODIC;
+    const int uk = ukind_internal(h->ukind);
+    for (int64_t n = 0; n < nsteps; ++n) {
+        StepArgs a = make_args(h, h->cur);
+        CK(h, lbm::launch_step(h->q, h->d.storage, uk, walls, h->cfg, a, h->st));
+        h->cur ^= 1;
+        h->t += 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec)
+{
+    if (!h) return fail(h, LBM_E_ARG, "NULL handle");
+    if (block < 32 || block > 1024 || block % 32 != 0 || (vec != 1 && vec != 2))
+        return fail(h, LBM_E_ARG, "block must be a multiple of 32 in [32, 1024], vec 1 or 2");
+    h->cfg.block = block;
+    h->cfg.vec = vec;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_get_time(lbm_cde_t h, int64_t* t_out)
+{
+    if (!h || !t_out) return fail(h, LBM_E_ARG, "NULL argument");
+    *t_out = h->t;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_get_phi(lbm_cde_t h, float* phi_dev)
+{
+    if (!h || !phi_dev) return fail(h, LBM_E_ARG, "NULL argument");
+    if (!h->ready) return fail(h, LBM_E_STATE, "no state yet");
+    StepArgs a = make_args(h, h->cur);
+    CK(h, lbm::launch_phi(h->q, h->d.storage, a, phi_dev, h->st));
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_sum_phi(lbm_cde_t h, double* out_host)
+{
+    if (!h || !out_host) return fail(h, LBM_E_ARG, "NULL argument");
+    if (!h->ready) return fail(h, LBM_E_STATE, "no state yet");
+    StepArgs a = make_args(h, h->cur);
+    CK(h, lbm::launch_sum(h->q, h->d.storage, a, h->partials, h->nparts, h->sum_dev, h->st));
+    CK(h, cudaMemcpyAsync(out_host, h->sum_dev, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    if (!std::isfinite(*out_host)) return fail(h, LBM_E_NONFINITE, "sum of phi is not finite");
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_sync(lbm_cde_t h)
+{
+    if (!h) return fail(h, LBM_E_ARG, "NULL handle");
+    CK(h, cudaStreamSynchronize(h->st));
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_state_bytes(lbm_cde_t h, size_t* bytes_out)
+{
+    if (!h || !bytes_out) return fail(h, LBM_E_ARG, "NULL argument");
+    *bytes_out = (size_t)h->ncell * h->elem * h->q + (h->neq ? (size_t)h->ncell * 4 : 0);
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_get_state(lbm_cde_t h, void* dst, int64_t* t_out)
+{
+    if (!h || !dst) return fail(h, LBM_E_ARG, "NULL argument");
+    if (!h->ready) return fail(h, LBM_E_STATE, "no state yet");
+    const size_t fb = (size_t)h->ncell * h->elem * h->q;
+    CK(h, cudaMemcpyAsync(dst, h->state[h->cur], fb, cudaMemcpyDefault, h->st));
+    if (h->neq)
+        CK(h, cudaMemcpyAsync(static_cast<char*>(dst) + fb, h->phi[h->cur], (size_t)h->ncell * 4,
+                              cudaMemcpyDefault, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    if (t_out) *t_out = h->t;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_set_state(lbm_cde_t h, const void* src, int64_t t)
+{
+    if (!h || !src || t < 0) return fail(h, LBM_E_ARG, "bad argument");
+    const size_t fb = (size_t)h->ncell * h->elem * h->q;
+    h->cur = 0;
+    CK(h, cudaMemcpyAsync(h->state[0], src, fb, cudaMemcpyDefault, h->st));
+    if (h->neq)
+        CK(h, cudaMemcpyAsync(h->phi[0], static_cast<const char*>(src) + fb, (size_t)h->ncell * 4,
+                              cudaMemcpyDefault, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    h->t = t;
+    h->ready = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_run_host(lbm_cde_t h, const float* phi0_host, int64_t nsteps, float* phi_out_host)
+{
+    if (!h || !phi0_host || !phi_out_host || nsteps < 0) return fail(h, LBM_E_ARG, "bad argument");
+    if (!h->phi_tmp) {
+        h->phi_tmp = static_cast<float*>(dev_alloc(h, (size_t)h->ncell * 4));
+        if (!h->phi_tmp) return fail(h, LBM_E_OOM, "phi buffer allocation failed");
+    }
+    const size_t bytes = (size_t)h->ncell * 4;
+    CK(h, cudaMemcpyAsync(h->phi_tmp, phi0_host, bytes, cudaMemcpyHostToDevice, h->st));
+    lbm_status s = lbm_cde_set_phi(h, h->phi_tmp);
+    if (s != LBM_OK) return s;
+    s = lbm_cde_step(h, nsteps);
+    if (s != LBM_OK) return s;
+    s = lbm_cde_get_phi(h, h->phi_tmp);
+    if (s != LBM_OK) return s;
+    CK(h, cudaMemcpyAsync(phi_out_host, h->phi_tmp, bytes, cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    return LBM_OK;
+}
+
+const char* lbm_cde_last_error(lbm_cde_t h)
+{
+    return h ? h->err.c_str() : g_create_err.c_str();
+}
+
+}  // extern "C"

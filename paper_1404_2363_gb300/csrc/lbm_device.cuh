@@ -1,0 +1,434 @@
+// Fused stream + collide kernels of the modified-MRT lattice Boltzmann model
+// for the convection-diffusion equation (Huang & Wu, arXiv:1404.2363), written
+// for sm_103a.
+//
+// One kernel launch = one time step for every cell:
+//   pull-stream f_i(x) = f'_i(x - e_i)                     (Eq. 5, pull form)
+//   wall rules on the y = 0 / y = ny-1 nodes                (Sec. 3.2 and variants)
+//   m = M f                                                 (Eq. 11-12 / A.2)
+//   m' = m - S (m - m^eq(phi, u))  with the modified S      (Eq. 13, 30-31 / A.5)
+//   f' = M^-1 m' = M^T diag(1/|M_k|^2) m'                   (Eq. 14, rows orthogonal)
+//
+// The path is bound by HBM bandwidth (about 1.5 flop per byte), so the design
+// goal is the minimum number of DRAM bytes per lattice update with coalesced
+// accesses: SoA planes, each warp reads 32 consecutive cells of a plane, the
+// x-shifted neighbour reads hit the sectors the neighbouring warps load, and
+// the y/z-shifted rows are reused from L2. M, M^-1 and S are compile-time
+// integer tables (folded into add/sub chains) and per-solver constants in
+// the kernel parameter bank; no tensor cores (a 9x9 or 15x15 integer
+// transform per cell is not a dense contraction).
+#pragma once
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Lattices. Velocities e_i of Eq. 2 (D2Q9) and Eq. A.1 in the order of the
+// moment rows of Eq. A.2 (D3Q15). Moment rows are written as the polynomials
+// of e that define them (density, energy, energy squared, momentum, energy
+// flux, stress components).
+// ---------------------------------------------------------------------------
+struct D2Q9 {
+    static constexpr int Q = 9;
+    static constexpr int DIM = 2;
+    __host__ __device__ static constexpr int ex(int i) {
+        return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ey(int i) {
+        return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ez(int) { return 0; }
+    __host__ __device__ static constexpr int M(int k, int i) {
+        const int x = ex(i), y = ey(i), e2 = x * x + y * y;
+        switch (k) {
+            case 0: return 1;
+            case 1: return -4 + 3 * e2;
+            case 2: return (8 - 21 * e2 + 9 * e2 * e2) / 2;
+            case 3: return x;
+            case 4: return (-5 + 3 * e2) * x;
+            case 5: return y;
+            case 6: return (-5 + 3 * e2) * y;
+            case 7: return x * x - y * y;
+            default: return x * y;
+        }
+    }
+};
+
+struct D3Q15 {
+    static constexpr int Q = 15;
+    static constexpr int DIM = 3;
+    // order: 0, +x, -x, +y, -y, +z, -z, then (+-1,+-1,+-1) with x fastest
+    // alternating and z = +1 for i = 7..10, -1 for i = 11..14
+    __host__ __device__ static constexpr int ex(int i) {
+        return (i == 1) ? 1 : (i == 2) ? -1 : (i >= 7) ? ((i % 2) ? 1 : -1) : 0;
+    }
+    __host__ __device__ static constexpr int ey(int i) {
+        return (i == 3) ? 1 : (i == 4) ? -1 : (i >= 7) ? ((((i - 7) / 2) % 2) ? -1 : 1) : 0;
+    }
+    __host__ __device__ static constexpr int ez(int i) {
+        return (i == 5) ? 1 : (i == 6) ? -1 : (i >= 7) ? ((i <= 10) ? 1 : -1) : 0;
+    }
+    __host__ __device__ static constexpr int M(int k, int i) {
+        const int x = ex(i), y = ey(i), z = ez(i), e2 = x * x + y * y + z * z;
+        switch (k) {
+            case 0: return 1;
+            case 1: return e2 - 2;
+            case 2: return (15 * e2 * e2 - 55 * e2 + 32) / 2;
+            case 3: return x;
+            case 4: return (5 * e2 - 13) * x / 2;
+            case 5: return y;
+            case 6: return (5 * e2 - 13) * y / 2;
+            case 7: return z;
+            case 8: return (5 * e2 - 13) * z / 2;
+            case 9: return 3 * x * x - e2;
+            case 10: return y * y - z * z;
+            case 11: return x * y;
+            case 12: return y * z;
+            case 13: return x * z;
+            default: return x * y * z;
+        }
+    }
+};
+
+template <class L>
+__host__ __device__ constexpr int row_norm2(int k) {
+    int s = 0;
+    for (int i = 0; i < L::Q; ++i) s += L::M(k, i) * L::M(k, i);
+    return s;
+}
+
+template <class L>
+__host__ __device__ constexpr int mirror_y(int i) {
+    for (int j = 0; j < L::Q; ++j)
+        if (L::ex(j) == L::ex(i) && L::ey(j) == -L::ey(i) && L::ez(j) == L::ez(i)) return j;
+    return -1;
+}
+
+template <class L>
+__host__ __device__ constexpr int opposite(int i) {
+    for (int j = 0; j < L::Q; ++j)
+        if (L::ex(j) == -L::ex(i) && L::ey(j) == -L::ey(i) && L::ez(j) == -L::ez(i)) return j;
+    return -1;
+}
+
+// weight class: 0 rest, 1 axis, 2 diagonal
+template <class L>
+__host__ __device__ constexpr int wclass(int i) {
+    const int n = L::ex(i) * L::ex(i) + L::ey(i) * L::ey(i) + L::ez(i) * L::ez(i);
+    return n == 0 ? 0 : (n == 1 ? 1 : 2);
+}
+
+// f^eq_i / phi = w_i + k_i e_i.u  (equilibria linear in u, Eq. 17)
+template <class L>
+__device__ __forceinline__ float feq_unit(const Coef& c, int i, float ux, float uy, float uz) {
+    const int w = wclass<L>(i);
+    const float eu = (float)L::ex(i) * ux + (float)L::ey(i) * uy + (float)L::ez(i) * uz;
+    if (w == 0) return c.w0;
+    if (w == 1) return fmaf(c.ka, eu, c.wa);
+    return fmaf(c.kd, eu, c.wd);
+}
+
+// ---------------------------------------------------------------------------
+// Collision in moment space for one node (Eq. 11, 13 with Eq. 31 / A.5, 14).
+// ---------------------------------------------------------------------------
+template <class L>
+__device__ __forceinline__ void collide(float (&f)[L::Q], float ux, float uy, float uz,
+                                        const Coef& c)
+{
+    constexpr int Q = L::Q;
+    float m[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        float acc = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int w = L::M(k, i);
+            if (w == 1) acc += f[i];
+            else if (w == -1) acc -= f[i];
+            else if (w != 0) acc = fmaf((float)w, f[i], acc);
+        }
+        m[k] = acc;
+    }
+    const float phi = m[0];
+    const float u[3] = {ux, uy, uz};
+    // non-equilibrium parts d = m - m^eq (Eq. 15 / A.3 with c1 = 1, c2 from Eq. 16 / A.4)
+    float d[Q];
+    d[0] = 0.f;
+    d[1] = m[1] - c.meq1 * phi;
+    d[2] = m[2] - c.meq2 * phi;
+#pragma unroll
+    for (int a = 0; a < L::DIM; ++a) {
+        d[3 + 2 * a] = m[3 + 2 * a] - phi * u[a];
+        d[4 + 2 * a] = m[4 + 2 * a] + phi * u[a];
+    }
+#pragma unroll
+    for (int k = 3 + 2 * L::DIM; k < Q; ++k) d[k] = m[k];
+    // relaxation m' = m - S d
+    float mp[Q];
+    mp[0] = m[0];
+    mp[1] = fmaf(-c.s[1], d[1], m[1]);
+    mp[2] = fmaf(-c.s[2], d[2], m[2]);
+#pragma unroll
+    for (int a = 0; a < L::DIM; ++a) {
+        float r = 0.f;
+#pragma unroll
+        for (int b = 0; b < L::DIM; ++b) {
+            r = fmaf(c.A[a * L::DIM + b], d[3 + 2 * b], r);
+            r = fmaf(c.C[a * L::DIM + b], d[4 + 2 * b], r);
+        }
+        mp[3 + 2 * a] = m[3 + 2 * a] - r;
+        mp[4 + 2 * a] = fmaf(-c.s[4 + 2 * a], d[4 + 2 * a], m[4 + 2 * a]);
+    }
+#pragma unroll
+    for (int k = 3 + 2 * L::DIM; k < Q; ++k) mp[k] = fmaf(-c.s[k], d[k], m[k]);
+    // f' = M^T diag(1 / |row|^2) m'
+#pragma unroll
+    for (int k = 0; k < Q; ++k) mp[k] *= 1.0f / (float)row_norm2<L>(k);
+    float rest = phi;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int w = L::M(k, i);
+            if (w == 1) acc += mp[k];
+            else if (w == -1) acc -= mp[k];
+            else if (w != 0) acc = fmaf((float)w, mp[k], acc);
+        }
+        f[i] = acc;
+        rest -= acc;
+    }
+    // The rest population closes the mass balance: sum_i f'_i = m'_0 = phi
+    // (row 0 of M^-1 m'). Taking it as phi minus the moving populations keeps
+    // FP32 rounding of the 1/|M_0|^2 factor from biasing the total mass.
+    f[0] = rest;
+}
+
+// ---------------------------------------------------------------------------
+// Storage helpers
+// ---------------------------------------------------------------------------
+template <int S> struct StT;
+template <> struct StT<ST_F32> { using T = float; };
+template <> struct StT<ST_F16> { using T = __half; };
+template <> struct StT<ST_BF16> { using T = __nv_bfloat16; };
+
+__device__ __forceinline__ float ldg_f(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldg_f(const __half* p) {
+    return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
+}
+__device__ __forceinline__ float ldg_f(const __nv_bfloat16* p) {
+    return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p))));
+}
+__device__ __forceinline__ void st_f(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st_f(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void st_f(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+__device__ __forceinline__ void sched_at(const StepArgs& a, long long k, int dim, float* s)
+{
+    s[0] = s[1] = s[2] = 1.f;
+    if (a.sched != nullptr && a.sched_len > 0) {
+        long long r = k % a.sched_len;
+        if (r < 0) r += a.sched_len;
+        for (int d = 0; d < dim; ++d) s[d] = __ldg(a.sched + r * dim + d);
+    }
+}
+
+template <int UK, int DIM>
+__device__ __forceinline__ void vel_at(const StepArgs& a, long long cell, int y, const float* s,
+                                       float& ux, float& uy, float& uz)
+{
+    ux = uy = uz = 0.f;
+    if (UK == U_FIELD) {
+        ux = __ldg(a.ua + cell) * s[0];
+        uy = __ldg(a.ua + a.ncell + cell) * s[1];
+        if (DIM == 3) uz = __ldg(a.ua + 2 * a.ncell + cell) * s[2];
+    } else if (UK == U_ROW) {
+        ux = __ldg(a.ua + y) * s[0];
+        uy = __ldg(a.ua + a.ny + y) * s[1];
+        if (DIM == 3) uz = __ldg(a.ua + 2 * a.ny + y) * s[2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The fused step kernel.
+// grid = (ceil(nx / (blockDim.x * VEC)), ny, nz); thread handles the cells
+// x = (blockIdx.x * VEC + j) * blockDim.x + threadIdx.x, j < VEC.
+// ---------------------------------------------------------------------------
+template <class L, int STORE, int UK, bool WALLS, int VEC>
+__global__ void __launch_bounds__(256) k_step(const StepArgs a)
+{
+    using T = typename StT<STORE>::T;
+    constexpr int Q = L::Q;
+    constexpr bool NEQ = (STORE != ST_F32);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long N = a.ncell;
+    const T* __restrict__ src = static_cast<const T*>(a.src);
+    T* __restrict__ dst = static_cast<T*>(a.dst);
+
+    // source rows for e_y = -1, 0, +1 (index ey + 1): row y - e_y, periodic
+    const int ys[3] = {y + 1 == ny ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};
+    const int zs[3] = {z + 1 == nz ? 0 : z + 1, z, z == 0 ? nz - 1 : z - 1};
+
+    float s_now[3], s_prev[3];
+    if (UK != U_NONE) {
+        sched_at(a, a.k, L::DIM, s_now);
+        sched_at(a, a.k - 1, L::DIM, s_prev);
+    }
+
+    float f[VEC][Q];
+    long long cell[VEC];
+    bool live[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        const int x = (blockIdx.x * VEC + j) * blockDim.x + threadIdx.x;
+        live[j] = x < nx;
+        const int xc = live[j] ? x : nx - 1;
+        const int xs[3] = {xc + 1 == nx ? 0 : xc + 1, xc, xc == 0 ? nx - 1 : xc - 1};
+        cell[j] = (long long)xc + (long long)nx * (y + (long long)ny * z);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const long long sc = (long long)xs[L::ex(i) + 1] +
+                                 (long long)nx * (ys[L::ey(i) + 1] + (long long)ny * zs[L::ez(i) + 1]);
+            float v = ldg_f(src + (long long)i * N + sc);
+            if (NEQ) {
+                float ux, uy, uz;
+                vel_at<UK, L::DIM>(a, sc, ys[L::ey(i) + 1], s_prev, ux, uy, uz);
+                v += __ldg(a.phi_src + sc) * feq_unit<L>(a.c, i, ux, uy, uz);
+            }
+            f[j][i] = v;
+        }
+    }
+
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        if (WALLS) {
+            const bool lo = (y == 0) && a.bc_lo != BC_PERIODIC;
+            const bool hi = (y == ny - 1) && a.bc_hi != BC_PERIODIC;
+            if (lo || hi) {
+                const int kind = lo ? a.bc_lo : a.bc_hi;
+                const int inward = lo ? 1 : -1;   // e_y of the populations entering from the wall
+                if (kind == BC_NOFLUX) {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i)
+                        if (L::ey(i) != 0 && ((L::ey(i) == 1) == lo)) f[j][i] = f[j][mirror_y<L>(i)];
+                } else if (kind == BC_BOUNCE) {
+                    float ux = 0.f, uy = 0.f, uz = 0.f;
+                    if (NEQ) vel_at<UK, L::DIM>(a, cell[j], y, s_prev, ux, uy, uz);
+#pragma unroll
+                    for (int i = 0; i < Q; ++i)
+                        if (L::ey(i) != 0 && ((L::ey(i) == 1) == lo)) {
+                            const int o = opposite<L>(i);
+                            float v = ldg_f(src + (long long)o * N + cell[j]);
+                            if (NEQ) v += __ldg(a.phi_src + cell[j]) * feq_unit<L>(a.c, o, ux, uy, uz);
+                            f[j][i] = v;
+                        }
+                } else {  // Dirichlet
+                    float ux, uy, uz;
+                    vel_at<UK, L::DIM>(a, cell[j], y, s_prev, ux, uy, uz);
+                    float known = 0.f, wk = 0.f;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        if (L::ey(i) == inward) wk += feq_unit<L>(a.c, i, ux, uy, uz);
+                        else known += f[j][i];
+                    }
+                    const float phiw = lo ? a.phiw_lo : a.phiw_hi;
+                    const float ps = (phiw - known) / wk;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i)
+                        if (L::ey(i) == inward) f[j][i] = ps * feq_unit<L>(a.c, i, ux, uy, uz);
+                }
+            }
+        }
+        float ux, uy, uz;
+        vel_at<UK, L::DIM>(a, cell[j], y, s_now, ux, uy, uz);
+        float phi = 0.f;
+        if (NEQ) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) phi += f[j][i];
+        }
+        collide<L>(f[j], ux, uy, uz, a.c);
+        if (!live[j]) continue;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float v = f[j][i];
+            if (NEQ) v -= phi * feq_unit<L>(a.c, i, ux, uy, uz);
+            st_f(dst + (long long)i * N + cell[j], v);
+        }
+        if (NEQ) a.phi_dst[cell[j]] = phi;
+    }
+}
+
+// f = f^eq(phi0, u(0)) (F32) or g = 0, phi = phi0 (16-bit forms)
+template <class L, int STORE, int UK>
+__global__ void k_init(const StepArgs a, const float* __restrict__ phi0)
+{
+    using T = typename StT<STORE>::T;
+    T* dst = static_cast<T*>(a.dst);
+    float s0[3];
+    sched_at(a, 0, L::DIM, s0);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)((c / a.nx) % a.ny);
+        float ux, uy, uz;
+        vel_at<UK, L::DIM>(a, c, y, s0, ux, uy, uz);
+        const float p = phi0[c];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const float v = (STORE == ST_F32) ? p * feq_unit<L>(a.c, i, ux, uy, uz) : 0.f;
+            st_f(dst + (long long)i * a.ncell + c, v);
+        }
+        if (STORE != ST_F32) a.phi_dst[c] = p;
+    }
+}
+
+template <class L, int STORE>
+__global__ void k_phi(const StepArgs a, float* __restrict__ out)
+{
+    using T = typename StT<STORE>::T;
+    const T* src = static_cast<const T*>(a.src);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (STORE != ST_F32) {
+            out[c] = a.phi_src[c];
+        } else {
+            float s = 0.f;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) s += ldg_f(src + (long long)i * a.ncell + c);
+            out[c] = s;
+        }
+    }
+}
+
+// Deterministic FP64 sum of phi: pass 1 writes one partial per block (fixed
+// grid-stride order, fixed shared-memory tree), pass 2 sums the partials in
+// index order in one block.
+template <class L, int STORE>
+__global__ void __launch_bounds__(256) k_sum1(const StepArgs a, double* __restrict__ partials)
+{
+    using T = typename StT<STORE>::T;
+    const T* src = static_cast<const T*>(a.src);
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (STORE != ST_F32) {
+            acc += (double)a.phi_src[c];
+        } else {
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) s += (double)ldg_f(src + (long long)i * a.ncell + c);
+            acc += s;
+        }
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+
+}  // namespace lbm

@@ -1,0 +1,62 @@
+// Internal declarations shared by the CUDA translation units of the solver.
+// Not part of the public C ABI (include/lbm_cde.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+enum Store { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
+enum UKind { U_NONE = 0, U_FIELD = 1, U_ROW = 2 };
+enum Bc { BC_PERIODIC = 0, BC_NOFLUX = 1, BC_BOUNCE = 2, BC_DIRICHLET = 3 };
+
+// Relaxation and equilibrium constants of one solver, passed by value to
+// every kernel (they live in the kernel parameter bank, i.e. constant cache).
+struct Coef {
+    // m^eq per unit phi for the two scalar moments:
+    //   D2Q9  (Eq. 15b-c): m1 = alpha1/4, m2 = alpha2/4
+    //   D3Q15 (Eq. A.3b-c): m1 = 5 alpha1/6, m2 = alpha2/24
+    float meq1, meq2;
+    float s[15];   // diagonal rates (entries 3, 5, 7 unused)
+    float A[9];    // flux block (row-major dim x dim)
+    // Coupling of flux row a to q-moment column b (Eq. 30a-b, A.5):
+    //   (A_ab / 2 - delta_ab) * s_{q-row of b}
+    float C[9];
+    // f^eq_i = phi * (w_i + k_i e_i.u), Eq. 17 / its D3Q15 counterpart
+    float w0, wa, wd, ka, kd;
+};
+
+struct StepArgs {
+    const void* src;      // state planes [q][ncell] (float or 16-bit)
+    void* dst;
+    const float* phi_src; // phi planes of the 16-bit forms
+    float* phi_dst;
+    const float* ua;      // velocity a(x) (FIELD: [dim][ncell], ROW: [dim][ny])
+    const float* sched;   // [sched_len][dim] or nullptr
+    long long sched_len;
+    long long k;          // this step computes f(k) and collides with u(k)
+    int nx, ny, nz;
+    long long ncell;
+    int bc_lo, bc_hi;
+    float phiw_lo, phiw_hi;
+    Coef c;
+};
+
+struct LaunchCfg {
+    int block;   // threads per block (multiple of 32)
+    int vec;     // cells per thread along x (1, 2 or 4)
+};
+
+// Kernel launchers (lbm_kernels.cu). Each returns the cudaError_t of the launch.
+cudaError_t launch_step(int q, int store, int ukind, bool walls, LaunchCfg cfg,
+                        const StepArgs& a, cudaStream_t st);
+cudaError_t launch_init(int q, int store, int ukind, const float* phi0, const StepArgs& a,
+                        cudaStream_t st);
+cudaError_t launch_phi(int q, int store, const StepArgs& a, float* phi_out, cudaStream_t st);
+cudaError_t launch_sum(int q, int store, const StepArgs& a, double* partials, int nblocks,
+                       double* out_dev, cudaStream_t st);
+
+}  // namespace lbm

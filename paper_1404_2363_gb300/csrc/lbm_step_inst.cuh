@@ -1,0 +1,34 @@
+// Launch dispatch for one (lattice, storage) pair of the fused step kernel.
+// Each step_*.cu translation unit includes this with LBM_LAT / LBM_STORE /
+// LBM_FN defined, so the template instantiations compile in parallel.
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+template <class L, int STORE, int UK, bool WALLS>
+static cudaError_t step_vec(LaunchCfg cfg, const StepArgs& a, cudaStream_t st)
+{
+    const int per = cfg.block * cfg.vec;
+    dim3 grid((unsigned)((a.nx + per - 1) / per), (unsigned)a.ny, (unsigned)a.nz);
+    dim3 block((unsigned)cfg.block);
+    if (cfg.vec == 2) k_step<L, STORE, UK, WALLS, 2><<<grid, block, 0, st>>>(a);
+    else k_step<L, STORE, UK, WALLS, 1><<<grid, block, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class L, int STORE, int UK>
+static cudaError_t step_w(bool walls, LaunchCfg cfg, const StepArgs& a, cudaStream_t st)
+{
+    return walls ? step_vec<L, STORE, UK, true>(cfg, a, st) : step_vec<L, STORE, UK, false>(cfg, a, st);
+}
+
+cudaError_t LBM_FN(int uk, bool walls, LaunchCfg cfg, const StepArgs& a, cudaStream_t st)
+{
+    switch (uk) {
+        case U_FIELD: return step_w<LBM_LAT, LBM_STORE, U_FIELD>(walls, cfg, a, st);
+        case U_ROW: return step_w<LBM_LAT, LBM_STORE, U_ROW>(walls, cfg, a, st);
+        default: return step_w<LBM_LAT, LBM_STORE, U_NONE>(walls, cfg, a, st);
+    }
+}
+
+}  // namespace lbm
