@@ -98,7 +98,7 @@ def lib(build_if_missing: bool = True):
     for name, argt in SIGNATURES.items():
         fn = getattr(L, name)
         fn.argtypes = argt
-        fn.restype = ctypes.c_char_p if name == "lbm_cde_last_error" else ctypes.c_int
+        fn.restype = ctypes.c_char_p if name.endswith("last_error") else ctypes.c_int
     _lib = L
     return L
 
