@@ -188,6 +188,36 @@ lbm_status lbm_cde_set_state(lbm_cde_t h, const void* src, int64_t t);
  * [ncell]. Synchronising. */
 lbm_status lbm_cde_run_host(lbm_cde_t h, const float* phi0_host, int64_t nsteps, float* phi_out_host);
 
+/* Allocation-free FP64 sum of phi over a raw state (no counterpart in the
+ * paper; an addition for callers that cannot allocate device memory, such as
+ * code running while a stream is captured into a CUDA graph or under a fixed
+ * memory budget). It performs no cudaMalloc/cudaFree or other allocation: the
+ * per-block partial sums live in a file-scope __device__ array of
+ * LBM_NOALLOC_MAX_PARTIALS doubles (128 KiB, held on every GPU that loads the
+ * library until the process exits).
+ *   state_dev : device pointer to a state laid out as lbm_cde_get_state writes
+ *               it (lattice planes of ncell elements, then for the 16-bit forms
+ *               an FP32 phi plane); 4-byte aligned, and for the 16-bit forms
+ *               q * ncell must be even so that the phi plane is aligned
+ *   lattice, storage : LBM_D2Q9 / LBM_D3Q15 and LBM_STORE_* of that state
+ *   ncell     : cells in the state, 1 .. LBM_NOALLOC_MAX_CELLS; larger states
+ *               are rejected with LBM_E_ARG
+ *   sum_dev   : device pointer to one double, overwritten with the sum
+ *   stream    : cudaStream_t (NULL: legacy stream); asynchronous
+ * The first call on a device resolves the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call before
+ * capturing a stream into a graph. Every call overwrites the partials it uses,
+ * so nothing needs clearing, but all calls on a GPU share the one array: calls
+ * whose kernels overlap on the GPU (unordered streams) race. Errors: LBM_E_ARG,
+ * LBM_E_CUDA; lbm_cde_noalloc_last_error() describes the last failure of the
+ * calling thread. */
+#define LBM_NOALLOC_MAX_PARTIALS 16384
+#define LBM_NOALLOC_CELLS_PER_BLOCK 4096
+#define LBM_NOALLOC_MAX_CELLS (16384LL * 4096LL)
+lbm_status lbm_cde_sum_state_noalloc(const void* state_dev, int32_t lattice, int32_t storage,
+                                     int64_t ncell, double* sum_dev, void* stream);
+const char* lbm_cde_noalloc_last_error(void);
+
 /* Message for the last error on this handle (static storage owned by the
  * handle; NULL handle gives the last creation error). */
 const char* lbm_cde_last_error(lbm_cde_t h);
