@@ -333,6 +333,38 @@ def e2e_run(store: str, steps: int):
             "note": f"one lbm_cde_run_host call of {steps} steps; per-step bytes are the call's copies / steps"}
 
 
+def adjoint_cost(store: str, ms_forward: float, nsteps: int = 400):
+    """Cost of the reverse sweep (checkpoint-segment recompute + adjoint kernels,
+    sqrt(N) checkpoints) per step, against one plain forward step: once for the
+    gradients of the inverse problem (dL/dD and dL/dphi0) and once with the
+    velocity-field gradient dL/da as well."""
+    import torch
+
+    s, wl, a, sched, phi0 = make_solver(store)
+    g = torch.ones((N_GRID, N_GRID), device="cuda", dtype=torch.float32)
+    s.forward_ckpt(phi0, 8)
+    s.backward(g, want_da=True)            # warm-up and allocation
+    torch.cuda.synchronize()
+    out = {"steps": nsteps, "checkpoint_every": int(np.ceil(np.sqrt(nsteps))),
+           "plain_forward_ms_per_step": ms_forward}
+    for tag, want_da in (("D_phi0", False), ("D_phi0_u", True)):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(s.stream)
+        s.forward_ckpt(phi0, nsteps)
+        e[1].record(s.stream)
+        s.backward(g, want_da=want_da)
+        e[2].record(s.stream)
+        torch.cuda.synchronize()
+        bwd = e[1].elapsed_time(e[2]) / nsteps
+        out[f"backward_ms_per_step[{tag}]"] = bwd
+        out[f"ratio_backward_vs_forward[{tag}]"] = bwd / ms_forward
+        out["forward_ckpt_ms_per_step"] = e[0].elapsed_time(e[1]) / nsteps
+    s.close()
+    out["bytes_per_lu_backward"] = {"recompute": 80, "adjoint": 116, "adjoint_with_dL_da": 132}
+    out["note"] = "backward = recompute of each checkpoint segment + one adjoint kernel per step"
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,6 +417,7 @@ def main():
                         "achieved_gbs": av, "frac_of_" + peak_kind + "_hbm": av / peak}
     torch.cuda.empty_cache()
 
+    adjoint = adjoint_cost(store, ms_forward=dt / args.steps * 1e3)
     e2e = e2e_run(store, args.steps)
     if rank != 0:
         barrier(world)
@@ -404,6 +437,7 @@ def main():
         "gpu_launches": args.steps,
         "clocks": cs.summary((t_wall0, t_wall1)),
         "variants": variants,
+        "adjoint": adjoint,
         "e2e": e2e,
         "sum_phi": mass_ok,
     }

@@ -188,6 +188,57 @@ lbm_status lbm_cde_set_state(lbm_cde_t h, const void* src, int64_t t);
  * [ncell]. Synchronising. */
 lbm_status lbm_cde_run_host(lbm_cde_t h, const float* phi0_host, int64_t nsteps, float* phi_out_host);
 
+/* ---- Differentiation (reverse-time adjoint) --------------------------------
+ * Not in the paper: for a fixed velocity one step is linear in f (Eq. 11-15),
+ * B_k = C_k P B_{k-1} with B the stored post-collision state, P the pull-stream
+ * with walls (Eq. 5, Sec. 3.2) and C_k = M^-1 [I - S (I - m^eq(1, u(k)) e_0^T)] M
+ * the collision (Eq. 13, 30-31 / A.5). The adjoint mu_k = dL/dB_k obeys
+ * mu_{k-1} = P^T C_k^T mu_k. Supported: FP32 storage, periodic / NOFLUX_NODE /
+ * BOUNCEBACK walls (LBM_E_UNSUPPORTED otherwise). */
+
+/* Number of FP64 gradient accumulators of one reverse step: 2 dim^2 + q
+ * (G_A[dim][dim], G_AC[dim][dim], G_diag[q]; see lbm_cde_grad_rates). */
+int32_t lbm_cde_adjoint_ngrad(int32_t lattice);
+
+/* One reverse step k >= 1 (the forward step that collided with u(k)):
+ *   mu_k_dev    : dL/dB_k, device FP32 [q][ncell]
+ *   mu_prev_dev : receives dL/dB_{k-1} (must not alias mu_k_dev)
+ *   f_prev_dev  : the forward state B_{k-1}, device FP32 [q][ncell]
+ *   grad_acc_dev: device FP64 [lbm_cde_adjoint_ngrad]; the partials
+ *                 G_A[a][b] += -sum (M^-T mu)_{j_a} (m - m^eq)_{j_b},
+ *                 G_AC[a][b] += -sum (M^-T mu)_{j_a} (m - m^eq)_{q_b},
+ *                 G_diag[r] += -sum (M^-T mu)_r (m - m^eq)_r are added
+ *                 (j_a = 3 + 2a flux rows, q_b = 4 + 2b energy-flux rows)
+ *   dL_da_dev   : NULL or device FP32 [dim][ncell]; += s(k) dL/du(x, k) for a
+ *                 LBM_U_FIELD velocity u = a(x) s(t)
+ * Asynchronous. Errors: LBM_E_ARG, LBM_E_UNSUPPORTED, LBM_E_STATE, LBM_E_OOM. */
+lbm_status lbm_cde_adjoint_step(lbm_cde_t h, int64_t k, const float* mu_k_dev, float* mu_prev_dev,
+                                const float* f_prev_dev, double* grad_acc_dev, float* dL_da_dev);
+
+/* Converts accumulated partials g (host, lbm_cde_adjoint_ngrad doubles) into
+ * dL/dD (host, dim x dim, every entry an independent variable; includes the
+ * tied rates s4 = sxx ... when tie_q_rates = 1) through A = (D/k + I/2)^-1, and
+ * dL/ds (host [15], the diagonal rates as independent variables). Either output
+ * may be NULL. */
+lbm_status lbm_cde_grad_rates(lbm_cde_t h, const double* g, double* dL_dD_host, double* dL_ds_host);
+
+/* Forward run for differentiation: f(0) = f^eq(phi0, u(0)), nsteps steps, keeping
+ * the state every `every` steps (0: ceil(sqrt(nsteps))) in handle-owned device
+ * memory (ceil(nsteps/every) + every - 1 states), then phi(nsteps) into phiN_dev
+ * (device FP32 [ncell], may be NULL). The handle's state afterwards is the one
+ * of step nsteps. */
+lbm_status lbm_cde_forward_ckpt(lbm_cde_t h, const float* phi0_dev, int64_t nsteps, int64_t every,
+                                float* phiN_dev);
+
+/* Reverse sweep of the last lbm_cde_forward_ckpt: recomputes each checkpoint
+ * segment, runs the adjoint steps and the initial-state term. Given
+ * dL/dphi(nsteps) (device FP32 [ncell]) it writes dL/dphi0 (device FP32
+ * [ncell]), dL/dD and dL/ds (host, see lbm_cde_grad_rates; may be NULL) and,
+ * if dL_da_dev is not NULL, overwrites it with dL/da (device FP32 [dim][ncell],
+ * LBM_U_FIELD velocity only). Synchronising. */
+lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dphi0_dev, double* dL_dD_host,
+                            double* dL_ds_host, float* dL_da_dev);
+
 /* Allocation-free FP64 sum of phi over a raw state (no counterpart in the
  * paper; an addition for callers that cannot allocate device memory, such as
  * code running while a stream is captured into a CUDA graph or under a fixed

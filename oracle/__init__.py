@@ -431,26 +431,29 @@ def converged_alpha(alpha_n, window: int = 100, tol: float = 1e-6):
     return None, float(a[-1])
 
 
-def adjoint_gradients(p: Params, phi0, nsteps: int, dL_dphiN, u=None):
-    """Reverse sweep of ``run`` for a velocity field that is constant in time.
-    Keeps every forward state (small grids only). Returns
+def adjoint_gradients(p: Params, phi0, nsteps: int, dL_dphiN, u=None, u_of_t=None):
+    """Reverse sweep of ``run`` keeping every forward state (small grids only).
+    The velocity is ``u`` (constant in time) or ``u_of_t(t)``. Returns
     (dL/dphi0 [ncell], dL/dD [dim x dim, entries treated independently],
-     dL/du [dim x ncell], dL/dS [q x q])."""
-    ua = _u_arr(p, u)
-    states = [init_eq(p, phi0, ua)]
+     dL/du [nsteps][dim x ncell] per collision time t (t = 0 includes the
+     dependence of the initial equilibrium on u(0)), dL/dS [q x q])."""
+    uf = (lambda t: _u_arr(p, u)) if u_of_t is None else (lambda t: _u_arr(p, u_of_t(t)))
+    states = [init_eq(p, phi0, uf(0))]
     post = np.empty_like(states[0])
-    for _ in range(nsteps):
-        states.append(step(p, states[-1], ua, post))
+    for t in range(nsteps):
+        states.append(step(p, states[-1], uf(t), post))
     lam = np.tile(np.asarray(dL_dphiN, dtype=np.float64).reshape(-1), p.q)
     dS = np.zeros((p.q, p.q))
-    du = np.zeros(p.dim * p.ncell)
+    du = np.zeros((max(nsteps, 1), p.dim * p.ncell))
     for n in range(nsteps - 1, -1, -1):
-        lam, dSn, dun = adjoint_step(p, lam, states[n], ua, want_dS=True, want_du=True)
+        lam, dSn, dun = adjoint_step(p, lam, states[n], uf(n), want_dS=True, want_du=True)
         dS += dSn
-        du += dun
-    dphi, dfdu = feq_jacobian(p, phi0, ua)
+        du[n] += dun
+    dphi, dfdu = feq_jacobian(p, phi0, uf(0))
     lam2 = lam.reshape(p.q, p.ncell)
     g_phi0 = (lam2 * dphi.reshape(p.q, p.ncell)).sum(axis=0)
-    g_u = du + (dfdu.reshape(p.dim, p.q, p.ncell) * lam2[None]).sum(axis=1).reshape(-1)
+    du[0] += (dfdu.reshape(p.dim, p.q, p.ncell) * lam2[None]).sum(axis=1).reshape(-1)
     gD = grad_D_from_s(p, s_gradients(p, dS)) if p.q == 9 else None
-    return g_phi0, gD, g_u.reshape(p.dim, p.ncell), dS
+    if u_of_t is None:
+        return g_phi0, gD, du.sum(axis=0).reshape(p.dim, p.ncell), dS
+    return g_phi0, gD, du.reshape(-1, p.dim, p.ncell), dS

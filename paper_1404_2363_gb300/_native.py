@@ -80,6 +80,11 @@ SIGNATURES = {
     "lbm_cde_set_state": [_P, _P, _I64],
     "lbm_cde_run_host": [_P, _P, _I64, _P],
     "lbm_cde_last_error": [_P],
+    "lbm_cde_adjoint_ngrad": [ctypes.c_int32],
+    "lbm_cde_adjoint_step": [_P, _I64, _P, _P, _P, _P, _P],
+    "lbm_cde_grad_rates": [_P, _DP, _DP, _DP],
+    "lbm_cde_forward_ckpt": [_P, _P, _I64, _I64, _P],
+    "lbm_cde_backward": [_P, _P, _P, _DP, _DP, _P],
     "lbm_cde_sum_state_noalloc": [_P, ctypes.c_int32, ctypes.c_int32, _I64, _P, _P],
     "lbm_cde_noalloc_last_error": [],
 }

@@ -1,0 +1,362 @@
+// Reverse-time (adjoint) step of the fused stream + collide kernel.
+//
+// For a fixed velocity field one step is linear in the distributions: with the
+// stored post-collision state B_k = C_k P B_{k-1} (P = pull-stream and walls,
+// C_k = M^-1 [I - S (I - v e_0^T)] M the collision with m^eq = phi v(u(k)),
+// Eq. 11-15, 30-31), the adjoint mu_k = dL/dB_k obeys
+//     mu_{k-1} = P^T C_k^T mu_k .
+// One thread per node y: it applies C_k^T to mu_k(y) in moment space,
+//     a = diag(1/|M_r|^2) M mu,   b = S^T a,   c = a - b + e_0 (v . b),   nu = M^T c,
+// then pushes nu_i to mu_{k-1,i}(y - e_i) (the transpose of the forward pull,
+// which read that same address), with the transposed wall rules. The forward
+// pre-collision state f_k = P B_{k-1} is pulled again to form the parameter
+// partials  dL/dS_rc = -sum a_r (m - m^eq)_c  and the velocity partials
+//     dL/du_a = phi (b_{j_a} - b_{q_a})   (j_a, q_a: flux and energy-flux rows).
+// Gradient partials are summed per warp in FP32, per block and over blocks in
+// FP64, in a fixed order.
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+template <class L>
+__host__ __device__ constexpr int ngrad() { return 2 * L::DIM * L::DIM + L::Q; }
+
+// Rows handled by one block of the adjoint kernel: the gradient partials of
+// ADJ_ROWS nodes per thread are summed in registers before the block reduction.
+constexpr int ADJ_ROWS = 8;
+
+template <class L, int UK, bool WALLS>
+__global__ void __launch_bounds__(256, 3) k_adjoint(const AdjArgs a)
+{
+    constexpr int Q = L::Q, DIM = L::DIM, NG = ngrad<L>();
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int z = blockIdx.z;
+    const long long N = a.ncell;
+    const bool live = x < nx;
+    const int xc = live ? x : nx - 1;
+    const int xs[3] = {xc + 1 == nx ? 0 : xc + 1, xc, xc == 0 ? nx - 1 : xc - 1};
+    const int zs[3] = {z + 1 == nz ? 0 : z + 1, z, z == 0 ? nz - 1 : z - 1};
+    const Coef& c = a.c;
+    float s_now[3];
+    sched_at(a.sched, a.sched_len, a.k, DIM, s_now);
+
+    float g[NG];
+#pragma unroll
+    for (int j = 0; j < NG; ++j) g[j] = 0.f;
+
+    const int y0 = blockIdx.y * ADJ_ROWS;
+#pragma unroll 1
+    for (int y = y0; y < y0 + ADJ_ROWS && y < ny; ++y) {
+        const int ys[3] = {y + 1 == ny ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};
+        const long long cell = (long long)xc + (long long)nx * (y + (long long)ny * z);
+        float mu[Q], f[Q];
+        long long tgt[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            tgt[i] = (long long)xs[L::ex(i) + 1] +
+                     (long long)nx * (ys[L::ey(i) + 1] + (long long)ny * zs[L::ez(i) + 1]);
+            mu[i] = __ldg(a.mu_in + (long long)i * N + cell);
+            f[i] = __ldg(a.fprev + (long long)i * N + tgt[i]);
+        }
+        const bool lo = WALLS && y == 0 && a.bc_lo != BC_PERIODIC;
+        const bool hi = WALLS && y == ny - 1 && a.bc_hi != BC_PERIODIC;
+        const int kind = lo ? a.bc_lo : a.bc_hi;
+        if (lo || hi) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if (L::ey(i) != 0 && ((L::ey(i) == 1) == lo)) {
+                    if (kind == BC_NOFLUX) f[i] = f[mirror_y<L>(i)];
+                    else f[i] = __ldg(a.fprev + (long long)opposite<L>(i) * N + cell);
+                }
+        }
+        float ux, uy, uz;
+        vel_at_p<UK, DIM>(a.ua, a.ncell, a.ny, cell, y, s_now, ux, uy, uz);
+        const float u[3] = {ux, uy, uz};
+
+        // forward non-equilibrium moments d = M f - m^eq(phi, u(k))
+        float m[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int w = L::M(k, i);
+                if (w == 1) acc += f[i];
+                else if (w == -1) acc -= f[i];
+                else if (w != 0) acc = fmaf((float)w, f[i], acc);
+            }
+            m[k] = acc;
+        }
+        const float phi = m[0];
+        float v[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) v[k] = 0.f;
+        v[0] = 1.f;
+        v[1] = c.meq1;
+        v[2] = c.meq2;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            v[3 + 2 * d] = u[d];
+            v[4 + 2 * d] = -u[d];
+        }
+        float dm[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) dm[k] = m[k] - phi * v[k];
+        dm[0] = 0.f;
+
+        // a = M^-T mu = diag(1/|M_r|^2) M mu
+        float av[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            float acc = 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int w = L::M(k, i);
+                if (w == 1) acc += mu[i];
+                else if (w == -1) acc -= mu[i];
+                else if (w != 0) acc = fmaf((float)w, mu[i], acc);
+            }
+            av[k] = acc * (1.0f / (float)row_norm2<L>(k));
+        }
+        // b = S^T a (S of Eq. 31 / A.5: diagonal rates, flux block A, couplings C)
+        float b[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) b[k] = c.s[k] * av[k];
+#pragma unroll
+        for (int bb = 0; bb < DIM; ++bb) {
+            float rf = 0.f, rq = 0.f;
+#pragma unroll
+            for (int aa = 0; aa < DIM; ++aa) {
+                rf = fmaf(c.A[aa * DIM + bb], av[3 + 2 * aa], rf);
+                rq = fmaf(c.C[aa * DIM + bb], av[3 + 2 * aa], rq);
+            }
+            b[3 + 2 * bb] = rf;
+            b[4 + 2 * bb] += rq;
+        }
+        float vb = 0.f;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) vb = fmaf(v[k], b[k], vb);
+        float cv[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) cv[k] = av[k] - b[k];
+        cv[0] += vb;
+        float nu[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const int w = L::M(k, i);
+                if (w == 1) acc += cv[k];
+                else if (w == -1) acc -= cv[k];
+                else if (w != 0) acc = fmaf((float)w, cv[k], acc);
+            }
+            nu[i] = acc;
+        }
+        if (!live) continue;
+
+        // velocity partials: u(x, k) = a(x) s(k)  =>  dL/da += s(k) dL/du(k)
+        if (UK == U_FIELD && a.du_acc != nullptr) {
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                float* p = a.du_acc + (long long)d * N + cell;
+                *p += phi * (b[3 + 2 * d] - b[4 + 2 * d]) * s_now[d];
+            }
+        }
+        // parameter partials (FP32 per thread over its ADJ_ROWS nodes)
+#pragma unroll
+        for (int aa = 0; aa < DIM; ++aa)
+#pragma unroll
+            for (int bb = 0; bb < DIM; ++bb) {
+                g[aa * DIM + bb] = fmaf(-av[3 + 2 * aa], dm[3 + 2 * bb], g[aa * DIM + bb]);
+                g[DIM * DIM + aa * DIM + bb] = fmaf(-av[3 + 2 * aa], dm[4 + 2 * bb], g[DIM * DIM + aa * DIM + bb]);
+            }
+#pragma unroll
+        for (int k = 1; k < Q; ++k) g[2 * DIM * DIM + k] = fmaf(-av[k], dm[k], g[2 * DIM * DIM + k]);
+
+        // push nu with the transposed wall rules
+        float* out = a.mu_out;
+        if (lo || hi) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (L::ey(i) != 0 && ((L::ey(i) == 1) == lo)) {          // entered from beyond the wall
+                    if (kind == BC_NOFLUX) nu[mirror_y<L>(i)] += nu[i];
+                    else out[(long long)opposite<L>(i) * N + cell] = nu[i];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (L::ey(i) != 0 && ((L::ey(i) == 1) == lo)) continue;
+                if (kind == BC_NOFLUX && L::ey(i) != 0) out[(long long)i * N + cell] = 0.f;  // left the domain
+                out[(long long)i * N + tgt[i]] = nu[i];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) out[(long long)i * N + tgt[i]] = nu[i];
+        }
+    }
+
+    // block reduction of the gradient partials: FP32 within a warp (FP64
+    // throughput is a small fraction of FP32 on this GPU), FP64 beyond
+#pragma unroll
+    for (int j = 0; j < NG; ++j)
+        for (int off = 16; off > 0; off >>= 1) g[j] += __shfl_down_sync(0xffffffffu, g[j], off);
+    __shared__ float red[8][NG];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < NG; ++j) red[warp][j] = g[j];
+    __syncthreads();
+    if ((int)threadIdx.x < NG) {
+        double s = 0.0;
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nw; ++w) s += (double)red[w][threadIdx.x];
+        const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+        const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
+        a.partials[threadIdx.x * nb + blk] = s;   // [NG][nblocks]: coalesced in the next pass
+    }
+}
+
+// Deterministic two-level sum of the per-block partials ([NG][nblocks]):
+// pass 2 reduces GRAD_CHUNKS contiguous chunks of every row in parallel,
+// pass 3 adds the chunk sums in index order to the running totals.
+constexpr int GRAD_CHUNKS = 32;
+
+__global__ void __launch_bounds__(256) k_grad_sum2(const double* __restrict__ partials, long long nblocks,
+                                                   double* __restrict__ p2)
+{
+    const int r = blockIdx.x, j = blockIdx.y;
+    const long long len = (nblocks + GRAD_CHUNKS - 1) / GRAD_CHUNKS;
+    const long long b0 = r * len;
+    const long long b1 = b0 + len < nblocks ? b0 + len : nblocks;
+    const double* row = partials + (long long)j * nblocks;
+    double s = 0.0;
+    for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) s += row[b];
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) p2[(long long)j * GRAD_CHUNKS + r] = red[0];
+}
+
+__global__ void k_grad_sum3(const double* __restrict__ p2, int ng, double* __restrict__ acc)
+{
+    const int j = threadIdx.x;
+    if (j >= ng) return;
+    double s = 0.0;
+    for (int r = 0; r < GRAD_CHUNKS; ++r) s += p2[j * GRAD_CHUNKS + r];
+    acc[j] += s;
+}
+
+// Gradients through the initial state B_0 = f^eq(phi0, u(0)):
+//   dL/dphi0 = sum_i mu_0,i f^eq_i(1, u),   dL/da += s(0) phi0 sum_i mu_0,i k_i e_i
+template <class L, int UK>
+__global__ void k_adjoint_init(const AdjArgs a, const float* __restrict__ phi0, float* __restrict__ dphi0)
+{
+    float s0[3];
+    sched_at(a.sched, a.sched_len, 0, L::DIM, s0);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)((c / a.nx) % a.ny);
+        float ux, uy, uz;
+        vel_at_p<UK, L::DIM>(a.ua, a.ncell, a.ny, c, y, s0, ux, uy, uz);
+        float gp = 0.f, gu[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const float m = __ldg(a.mu_in + (long long)i * a.ncell + c);
+            gp = fmaf(m, feq_unit<L>(a.c, i, ux, uy, uz), gp);
+            const float k = wclass<L>(i) == 1 ? a.c.ka : (wclass<L>(i) == 2 ? a.c.kd : 0.f);
+            gu[0] = fmaf(m * k, (float)L::ex(i), gu[0]);
+            gu[1] = fmaf(m * k, (float)L::ey(i), gu[1]);
+            gu[2] = fmaf(m * k, (float)L::ez(i), gu[2]);
+        }
+        dphi0[c] = gp;
+        if (UK == U_FIELD && a.du_acc != nullptr) {
+            const float p = phi0[c];
+            for (int d = 0; d < L::DIM; ++d) a.du_acc[(long long)d * a.ncell + c] += s0[d] * p * gu[d];
+        }
+    }
+}
+
+// mu_N,i = dL/dphi_N for every i (phi_N = sum_i B_N,i)
+__global__ void k_adjoint_seed(const float* __restrict__ g, float* __restrict__ mu, long long ncell, int q)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+         c += (long long)gridDim.x * blockDim.x) {
+        const float v = g[c];
+        for (int i = 0; i < q; ++i) mu[(long long)i * ncell + c] = v;
+    }
+}
+
+template <class L, int UK>
+static cudaError_t adj_w(bool walls, const AdjArgs& a, cudaStream_t st, long long* nblocks)
+{
+    dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)((a.ny + ADJ_ROWS - 1) / ADJ_ROWS), (unsigned)a.nz);
+    *nblocks = (long long)grid.x * grid.y * grid.z;
+    if (walls) k_adjoint<L, UK, true><<<grid, 256, 0, st>>>(a);
+    else k_adjoint<L, UK, false><<<grid, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    constexpr int NG = ngrad<L>();
+    double* p2 = a.partials + *nblocks * NG;
+    k_grad_sum2<<<dim3(GRAD_CHUNKS, NG), 256, 0, st>>>(a.partials, *nblocks, p2);
+    k_grad_sum3<<<1, 64, 0, st>>>(p2, NG, a.grad_acc);
+    return cudaGetLastError();
+}
+
+template <class L>
+static cudaError_t adj_u(int uk, bool walls, const AdjArgs& a, cudaStream_t st, long long* nb)
+{
+    switch (uk) {
+        case U_FIELD: return adj_w<L, U_FIELD>(walls, a, st, nb);
+        case U_ROW: return adj_w<L, U_ROW>(walls, a, st, nb);
+        default: return adj_w<L, U_NONE>(walls, a, st, nb);
+    }
+}
+
+cudaError_t launch_adjoint(int q, int ukind, bool walls, const AdjArgs& a, cudaStream_t st)
+{
+    long long nb = 0;
+    return q == 9 ? adj_u<D2Q9>(ukind, walls, a, st, &nb) : adj_u<D3Q15>(ukind, walls, a, st, &nb);
+}
+
+long long adjoint_partials_size(int q, long long nx, long long ny, long long nz)
+{
+    const long long nb = ((nx + 255) / 256) * ((ny + ADJ_ROWS - 1) / ADJ_ROWS) * nz;
+    return (nb + GRAD_CHUNKS) * (q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>());
+}
+
+int adjoint_ngrad(int q) { return q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>(); }
+
+template <class L>
+static cudaError_t init_u(int uk, const AdjArgs& a, const float* phi0, float* dphi0, cudaStream_t st)
+{
+    long long b = (a.ncell + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    switch (uk) {
+        case U_FIELD: k_adjoint_init<L, U_FIELD><<<(int)b, 256, 0, st>>>(a, phi0, dphi0); break;
+        case U_ROW: k_adjoint_init<L, U_ROW><<<(int)b, 256, 0, st>>>(a, phi0, dphi0); break;
+        default: k_adjoint_init<L, U_NONE><<<(int)b, 256, 0, st>>>(a, phi0, dphi0); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_init(int q, int ukind, const AdjArgs& a, const float* phi0, float* dphi0,
+                                cudaStream_t st)
+{
+    return q == 9 ? init_u<D2Q9>(ukind, a, phi0, dphi0, st) : init_u<D3Q15>(ukind, a, phi0, dphi0, st);
+}
+
+cudaError_t launch_adjoint_seed(const float* g, float* mu, long long ncell, int q, cudaStream_t st)
+{
+    long long b = (ncell + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    k_adjoint_seed<<<(int)b, 256, 0, st>>>(g, mu, ncell, q);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,11 +1,13 @@
 // Host runtime behind the C ABI of include/lbm_cde.h: handle, buffers,
 // parameter derivation (D -> A, Eq. 36 / A.6), ping-pong stepping, reductions,
 // checkpoints. Every entry point catches its own failures and returns a status.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/lbm_cde.h"
 #include "lbm_internal.cuh"
@@ -40,6 +42,16 @@ struct lbm_cde_s {
     LaunchCfg cfg{256, 1};
     cudaStream_t st = nullptr;
     std::string err;
+    // adjoint: checkpoints of the forward run, segment recompute buffer, adjoint states
+    std::vector<void*> ck;
+    int64_t ck_every = 0, ck_nsteps = 0;
+    void* seg = nullptr;
+    int64_t seg_states = 0;
+    float* mu[2] = {nullptr, nullptr};
+    double* adj_partials = nullptr;
+    double* grad_acc = nullptr;
+    float* phi0_saved = nullptr;
+    bool have_fwd = false;
 };
 
 static thread_local std::string g_create_err;
@@ -314,6 +326,12 @@ lbm_status lbm_cde_destroy(lbm_cde_t h)
     }
     dev_free(h, h->phi_tmp);
     dev_free(h, h->partials);
+    for (void* p : h->ck) dev_free(h, p);
+    dev_free(h, h->seg);
+    dev_free(h, h->mu[0]);
+    dev_free(h, h->mu[1]);
+    dev_free(h, h->adj_partials);
+    dev_free(h, h->phi0_saved);
     delete h;
     return LBM_OK;
 }
@@ -495,6 +513,228 @@ lbm_status lbm_cde_run_host(lbm_cde_t h, const float* phi0_host, int64_t nsteps,
     CK(h, cudaMemcpyAsync(phi_out_host, h->phi_tmp, bytes, cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaStreamSynchronize(h->st));
     return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint
+// ---------------------------------------------------------------------------
+int32_t lbm_cde_adjoint_ngrad(int32_t lattice) { return lbm::adjoint_ngrad(lattice == LBM_D3Q15 ? 15 : 9); }
+
+static lbm_status adjoint_supported(lbm_cde_t h)
+{
+    if (h->d.storage != LBM_STORE_F32)
+        return fail(h, LBM_E_UNSUPPORTED, "the adjoint needs FP32 state storage");
+    if (h->d.bc_lo_y == LBM_BC_DIRICHLET || h->d.bc_hi_y == LBM_BC_DIRICHLET)
+        return fail(h, LBM_E_UNSUPPORTED, "the adjoint does not support Dirichlet walls");
+    if (!h->d_set) return fail(h, LBM_E_STATE, "set_D must come first");
+    return LBM_OK;
+}
+
+static lbm_status ensure_adjoint_buffers(lbm_cde_t h)
+{
+    const size_t sb = (size_t)h->ncell * 4 * h->q;
+    for (int b = 0; b < 2; ++b)
+        if (!h->mu[b]) {
+            h->mu[b] = static_cast<float*>(dev_alloc(h, sb));
+            if (!h->mu[b]) return fail(h, LBM_E_OOM, "adjoint state allocation failed");
+        }
+    if (!h->adj_partials) {
+        const long long np = lbm::adjoint_partials_size(h->q, h->d.nx, h->d.ny, h->d.nz);
+        const int ng = lbm::adjoint_ngrad(h->q);
+        h->adj_partials = static_cast<double*>(dev_alloc(h, sizeof(double) * (np + ng)));
+        if (!h->adj_partials) return fail(h, LBM_E_OOM, "adjoint scratch allocation failed");
+        h->grad_acc = h->adj_partials + np;
+    }
+    return LBM_OK;
+}
+
+static lbm::AdjArgs make_adj(lbm_cde_t h, int64_t k, const float* mu_in, float* mu_out, const float* fprev,
+                             float* du, double* grad_acc)
+{
+    lbm::AdjArgs a{};
+    a.mu_in = mu_in;
+    a.mu_out = mu_out;
+    a.fprev = fprev;
+    a.ua = h->ua;
+    a.sched = h->sched;
+    a.sched_len = h->sched_len;
+    a.k = k;
+    a.nx = (int)h->d.nx;
+    a.ny = (int)h->d.ny;
+    a.nz = (int)h->d.nz;
+    a.ncell = h->ncell;
+    a.bc_lo = h->d.bc_lo_y;
+    a.bc_hi = h->d.bc_hi_y;
+    a.c = h->coef;
+    a.du_acc = du;
+    a.partials = h->adj_partials;
+    a.grad_acc = grad_acc;
+    return a;
+}
+
+lbm_status lbm_cde_adjoint_step(lbm_cde_t h, int64_t k, const float* mu_k_dev, float* mu_prev_dev,
+                                const float* f_prev_dev, double* grad_acc_dev, float* dL_da_dev)
+{
+    if (!h || !mu_k_dev || !mu_prev_dev || !f_prev_dev || !grad_acc_dev || k < 1)
+        return fail(h, LBM_E_ARG, "bad argument");
+    if (mu_k_dev == mu_prev_dev) return fail(h, LBM_E_ARG, "mu_k and mu_prev must not alias");
+    lbm_status s = adjoint_supported(h);
+    if (s != LBM_OK) return s;
+    if (dL_da_dev && h->ukind != LBM_U_FIELD)
+        return fail(h, LBM_E_UNSUPPORTED, "velocity gradients need a velocity field (LBM_U_FIELD)");
+    s = ensure_adjoint_buffers(h);
+    if (s != LBM_OK) return s;
+    lbm::AdjArgs a = make_adj(h, k, mu_k_dev, mu_prev_dev, f_prev_dev, dL_da_dev, grad_acc_dev);
+    CK(h, lbm::launch_adjoint(h->q, ukind_internal(h->ukind), h->d.bc_lo_y != LBM_BC_PERIODIC, a, h->st));
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_grad_rates(lbm_cde_t h, const double* g, double* dL_dD_host, double* dL_ds_host)
+{
+    if (!h || !g) return fail(h, LBM_E_ARG, "NULL argument");
+    const int n = h->dim, q = h->q;
+    const double* GA = g;
+    const double* GAC = g + n * n;
+    const double* Gd = g + 2 * n * n;
+    double s[15];
+    for (int k = 0; k < 15; ++k) s[k] = h->coef.s[k];
+    double dA[9] = {0}, ds[15] = {0};
+    // S entries (Eq. 30-31 / A.5): A_ab, C_ab = (A_ab/2 - delta_ab) s_{q_b}, diagonal s_k
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+            const double sq = s[4 + 2 * b];
+            dA[a * n + b] = GA[a * n + b] + GAC[a * n + b] * sq / 2.0;
+            ds[4 + 2 * b] += GAC[a * n + b] * (h->A[a * n + b] / 2.0 - (a == b ? 1.0 : 0.0));
+        }
+    for (int k = 1; k < q; ++k) {
+        const bool flux = (k == 3 || k == 5 || (n == 3 && k == 7));
+        if (!flux) ds[k] += Gd[k];
+    }
+    if (dL_ds_host)
+        for (int k = 0; k < 15; ++k) dL_ds_host[k] = k < q ? ds[k] : 0.0;
+    if (dL_dD_host) {
+        // tied q-rates s_{q_b} = A_bb are functions of D as well
+        if (h->d.tie_q_rates)
+            for (int b = 0; b < n; ++b) dA[b * n + b] += ds[4 + 2 * b];
+        // A = (D/k + I/2)^-1  =>  dL/dD = -(1/k) A^T dL/dA A^T
+        const double kf = diffusion_factor(q, h->alpha1, h->alpha2);
+        double T[9] = {0};
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double acc = 0.0;
+                for (int l = 0; l < n; ++l) acc += h->A[l * n + i] * dA[l * n + j];   // (A^T dA)_ij
+                T[i * n + j] = acc;
+            }
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double acc = 0.0;
+                for (int l = 0; l < n; ++l) acc += T[i * n + l] * h->A[j * n + l];      // (T A^T)_ij
+                dL_dD_host[i * n + j] = -acc / kf;
+            }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_forward_ckpt(lbm_cde_t h, const float* phi0_dev, int64_t nsteps, int64_t every,
+                                float* phiN_dev)
+{
+    if (!h || !phi0_dev || nsteps < 1 || every < 0) return fail(h, LBM_E_ARG, "bad argument");
+    lbm_status s = adjoint_supported(h);
+    if (s != LBM_OK) return s;
+    if (every == 0) {
+        every = (int64_t)std::ceil(std::sqrt((double)nsteps));
+        if (every < 1) every = 1;
+    }
+    const int64_t nck = (nsteps + every - 1) / every;
+    const size_t sb = (size_t)h->ncell * 4 * h->q;
+    if ((int64_t)h->ck.size() != nck) {
+        for (void* p : h->ck) dev_free(h, p);
+        h->ck.assign(nck, nullptr);
+        for (int64_t j = 0; j < nck; ++j) {
+            h->ck[j] = dev_alloc(h, sb);
+            if (!h->ck[j]) return fail(h, LBM_E_OOM, "checkpoint allocation failed");
+        }
+    }
+    const int64_t segn = every > 1 ? every - 1 : 1;
+    if (h->seg_states != segn) {
+        dev_free(h, h->seg);
+        h->seg = dev_alloc(h, sb * segn);
+        if (!h->seg) return fail(h, LBM_E_OOM, "segment allocation failed");
+        h->seg_states = segn;
+    }
+    if (!h->phi0_saved) {
+        h->phi0_saved = static_cast<float*>(dev_alloc(h, (size_t)h->ncell * 4));
+        if (!h->phi0_saved) return fail(h, LBM_E_OOM, "allocation failed");
+    }
+    CK(h, cudaMemcpyAsync(h->phi0_saved, phi0_dev, (size_t)h->ncell * 4, cudaMemcpyDeviceToDevice, h->st));
+    s = lbm_cde_set_phi(h, phi0_dev);
+    if (s != LBM_OK) return s;
+    CK(h, cudaMemcpyAsync(h->ck[0], h->state[h->cur], sb, cudaMemcpyDeviceToDevice, h->st));
+    for (int64_t k = 1; k <= nsteps; ++k) {
+        s = lbm_cde_step(h, 1);
+        if (s != LBM_OK) return s;
+        if (k % every == 0 && k < nsteps)
+            CK(h, cudaMemcpyAsync(h->ck[k / every], h->state[h->cur], sb, cudaMemcpyDeviceToDevice, h->st));
+    }
+    if (phiN_dev) {
+        s = lbm_cde_get_phi(h, phiN_dev);
+        if (s != LBM_OK) return s;
+    }
+    h->ck_every = every;
+    h->ck_nsteps = nsteps;
+    h->have_fwd = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dphi0_dev, double* dL_dD_host,
+                            double* dL_ds_host, float* dL_da_dev)
+{
+    if (!h || !dL_dphiN_dev || !dL_dphi0_dev) return fail(h, LBM_E_ARG, "NULL argument");
+    if (!h->have_fwd) return fail(h, LBM_E_STATE, "lbm_cde_forward_ckpt must come first");
+    lbm_status s = adjoint_supported(h);
+    if (s != LBM_OK) return s;
+    if (dL_da_dev && h->ukind != LBM_U_FIELD)
+        return fail(h, LBM_E_UNSUPPORTED, "velocity gradients need a velocity field (LBM_U_FIELD)");
+    s = ensure_adjoint_buffers(h);
+    if (s != LBM_OK) return s;
+    const int ng = lbm::adjoint_ngrad(h->q);
+    const size_t sb = (size_t)h->ncell * 4 * h->q;
+    const int uk = ukind_internal(h->ukind);
+    const bool walls = h->d.bc_lo_y != LBM_BC_PERIODIC;
+    CK(h, cudaMemsetAsync(h->grad_acc, 0, sizeof(double) * ng, h->st));
+    if (dL_da_dev) CK(h, cudaMemsetAsync(dL_da_dev, 0, (size_t)h->ncell * 4 * h->dim, h->st));
+    CK(h, lbm::launch_adjoint_seed(dL_dphiN_dev, h->mu[0], h->ncell, h->q, h->st));
+    int cur = 0;
+    const int64_t K = h->ck_every, Nst = h->ck_nsteps;
+    const int64_t nck = (int64_t)h->ck.size();
+    auto seg_state = [&](int64_t j, int64_t t) -> float* {   // B_{jK + t}
+        if (t == 0) return static_cast<float*>(h->ck[j]);
+        return reinterpret_cast<float*>(static_cast<char*>(h->seg) + sb * (t - 1));
+    };
+    for (int64_t j = nck - 1; j >= 0; --j) {
+        const int64_t start = j * K;
+        const int64_t end = std::min(start + K, Nst);
+        // recompute B_{start+1} .. B_{end-1} from the checkpoint
+        for (int64_t t = 1; t < end - start; ++t) {
+            StepArgs a = make_args(h, 0);
+            a.src = seg_state(j, t - 1);
+            a.dst = seg_state(j, t);
+            a.k = start + t;
+            CK(h, lbm::launch_step(h->q, LBM_STORE_F32, uk, walls, h->cfg, a, h->st));
+        }
+        for (int64_t k = end; k > start; --k) {
+            lbm::AdjArgs a = make_adj(h, k, h->mu[cur], h->mu[1 - cur], seg_state(j, k - 1 - start), dL_da_dev,
+                                      h->grad_acc);
+            CK(h, lbm::launch_adjoint(h->q, uk, walls, a, h->st));
+            cur ^= 1;
+        }
+    }
+    lbm::AdjArgs a0 = make_adj(h, 0, h->mu[cur], nullptr, nullptr, dL_da_dev, h->grad_acc);
+    CK(h, lbm::launch_adjoint_init(h->q, uk, a0, h->phi0_saved, dL_dphi0_dev, h->st));
+    double g[33];
+    CK(h, cudaMemcpyAsync(g, h->grad_acc, sizeof(double) * ng, cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    return lbm_cde_grad_rates(h, g, dL_dD_host, dL_ds_host);
 }
 
 const char* lbm_cde_last_error(lbm_cde_t h)

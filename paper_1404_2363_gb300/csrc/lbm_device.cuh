@@ -223,13 +223,36 @@ __device__ __forceinline__ void st_f(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st_f(__half* p, float v) { *p = __float2half_rn(v); }
 __device__ __forceinline__ void st_f(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
-__device__ __forceinline__ void sched_at(const StepArgs& a, long long k, int dim, float* s)
+// Schedule multipliers s(k) (t mod sched_len), 1 when there is no schedule.
+__device__ __forceinline__ void sched_at(const float* sched, long long len, long long k, int dim, float* s)
 {
     s[0] = s[1] = s[2] = 1.f;
-    if (a.sched != nullptr && a.sched_len > 0) {
-        long long r = k % a.sched_len;
-        if (r < 0) r += a.sched_len;
-        for (int d = 0; d < dim; ++d) s[d] = __ldg(a.sched + r * dim + d);
+    if (sched != nullptr && len > 0) {
+        long long r = k % len;
+        if (r < 0) r += len;
+        for (int d = 0; d < dim; ++d) s[d] = __ldg(sched + r * dim + d);
+    }
+}
+
+__device__ __forceinline__ void sched_at(const StepArgs& a, long long k, int dim, float* s)
+{
+    sched_at(a.sched, a.sched_len, k, dim, s);
+}
+
+// u(x, k) = a(x) s(k) for a field, a(y) s(k) for a row profile, 0 otherwise.
+template <int UK, int DIM>
+__device__ __forceinline__ void vel_at_p(const float* ua, long long ncell, int ny, long long cell, int y,
+                                         const float* s, float& ux, float& uy, float& uz)
+{
+    ux = uy = uz = 0.f;
+    if (UK == U_FIELD) {
+        ux = __ldg(ua + cell) * s[0];
+        uy = __ldg(ua + ncell + cell) * s[1];
+        if (DIM == 3) uz = __ldg(ua + 2 * ncell + cell) * s[2];
+    } else if (UK == U_ROW) {
+        ux = __ldg(ua + y) * s[0];
+        uy = __ldg(ua + ny + y) * s[1];
+        if (DIM == 3) uz = __ldg(ua + 2 * ny + y) * s[2];
     }
 }
 
@@ -237,16 +260,7 @@ template <int UK, int DIM>
 __device__ __forceinline__ void vel_at(const StepArgs& a, long long cell, int y, const float* s,
                                        float& ux, float& uy, float& uz)
 {
-    ux = uy = uz = 0.f;
-    if (UK == U_FIELD) {
-        ux = __ldg(a.ua + cell) * s[0];
-        uy = __ldg(a.ua + a.ncell + cell) * s[1];
-        if (DIM == 3) uz = __ldg(a.ua + 2 * a.ncell + cell) * s[2];
-    } else if (UK == U_ROW) {
-        ux = __ldg(a.ua + y) * s[0];
-        uy = __ldg(a.ua + a.ny + y) * s[1];
-        if (DIM == 3) uz = __ldg(a.ua + 2 * a.ny + y) * s[2];
-    }
+    vel_at_p<UK, DIM>(a.ua, a.ncell, a.ny, cell, y, s, ux, uy, uz);
 }
 
 // ---------------------------------------------------------------------------

@@ -45,6 +45,24 @@ struct StepArgs {
     Coef c;
 };
 
+// One reverse-time step (lbm_adjoint.cu).
+struct AdjArgs {
+    const float* mu_in;   // adjoint of the post-collision state B_k [q][ncell]
+    float* mu_out;        // adjoint of B_{k-1}
+    const float* fprev;   // forward state B_{k-1} (FP32) [q][ncell]
+    const float* ua;
+    const float* sched;
+    long long sched_len;
+    long long k;          // the forward step being reversed (collision with u(k))
+    int nx, ny, nz;
+    long long ncell;
+    int bc_lo, bc_hi;
+    Coef c;
+    float* du_acc;        // dL/da accumulator [dim][ncell] (FIELD velocity) or nullptr
+    double* partials;     // per-block gradient partials [nblocks][ngrad]
+    double* grad_acc;     // [ngrad] running sums: G_A[dim][dim], G_AC[dim][dim], G_diag[q]
+};
+
 struct LaunchCfg {
     int block;   // threads per block (multiple of 32)
     int vec;     // cells per thread along x (1, 2 or 4)
@@ -58,5 +76,12 @@ cudaError_t launch_init(int q, int store, int ukind, const float* phi0, const St
 cudaError_t launch_phi(int q, int store, const StepArgs& a, float* phi_out, cudaStream_t st);
 cudaError_t launch_sum(int q, int store, const StepArgs& a, double* partials, int nblocks,
                        double* out_dev, cudaStream_t st);
+
+cudaError_t launch_adjoint(int q, int ukind, bool walls, const AdjArgs& a, cudaStream_t st);
+cudaError_t launch_adjoint_init(int q, int ukind, const AdjArgs& a, const float* phi0, float* dphi0,
+                                cudaStream_t st);
+cudaError_t launch_adjoint_seed(const float* g, float* mu, long long ncell, int q, cudaStream_t st);
+long long adjoint_partials_size(int q, long long nx, long long ny, long long nz);
+int adjoint_ngrad(int q);
 
 }  // namespace lbm

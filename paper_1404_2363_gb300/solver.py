@@ -176,6 +176,29 @@ class Solver:
     def set_state(self, buf, t):
         self._ck(self.L.lbm_cde_set_state(self.h, buf.data_ptr(), int(t)), "lbm_cde_set_state")
 
+    # -- differentiation -------------------------------------------------
+    def forward_ckpt(self, phi0, nsteps, every=0, out=None):
+        """phi after nsteps from f^eq(phi0, u(0)), keeping checkpoints for backward()."""
+        phi0 = phi0.to(self.device, torch.float32).contiguous()
+        self._phi0 = phi0
+        if out is None:
+            out = torch.empty(self.shape, device=self.device, dtype=torch.float32)
+        self._ck(self.L.lbm_cde_forward_ckpt(self.h, phi0.data_ptr(), int(nsteps), int(every), out.data_ptr()),
+                 "lbm_cde_forward_ckpt")
+        return out
+
+    def backward(self, dL_dphiN, want_da=False):
+        """Gradients of the last forward_ckpt: (dL/dphi0, dL/dD (numpy), dL/ds (numpy), dL/da or None)."""
+        g = dL_dphiN.to(self.device, torch.float32).contiguous()
+        dphi0 = torch.empty(self.shape, device=self.device, dtype=torch.float32)
+        dD = np.zeros(self.dim * self.dim)
+        ds = np.zeros(15)
+        da = torch.empty((self.dim,) + self.shape, device=self.device, dtype=torch.float32) if want_da else None
+        self._ck(self.L.lbm_cde_backward(self.h, g.data_ptr(), dphi0.data_ptr(), dD.ctypes.data_as(N._DP),
+                                         ds.ctypes.data_as(N._DP), da.data_ptr() if da is not None else None),
+                 "lbm_cde_backward")
+        return dphi0, dD.reshape(self.dim, self.dim), ds, da
+
     def run_host(self, phi0: np.ndarray, nsteps: int, out: np.ndarray | None = None):
         phi0 = np.ascontiguousarray(phi0, dtype=np.float32)
         if out is None:

@@ -1,0 +1,185 @@
+"""GPU adjoint (reverse-time kernels behind lbm_cde_backward / torch.autograd)
+against the FP64 oracle adjoint and central finite differences of the oracle.
+
+The oracle adjoint is pinned separately (tests/test_oracle_adjoint.py: it equals
+the transpose of the assembled one-step matrix and matches FP64 central
+differences). Here the loss is L = sum_x g(x) phi_N(x) with a fixed random g,
+so both sides differentiate the same functional.
+"""
+import numpy as np
+import pytest
+import torch
+
+from _common import Case, oracle_params, rel_l2
+from paper_1404_2363_gb300.solver import Solver
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_grads(case, phi0, a, sched, g, every=0):
+    s = Solver(nx=case.nx, ny=case.ny, bc=case.bc)
+    s.set_D(case.D)
+    if a is not None:
+        s.set_velocity(torch.from_numpy(a).cuda(), None if sched is None else torch.from_numpy(sched).cuda())
+    phiN = s.forward_ckpt(torch.from_numpy(phi0).cuda(), case.steps, every)
+    dphi0, dD, ds, da = s.backward(torch.from_numpy(g.astype(np.float32)).cuda(), want_da=a is not None)
+    out = (phiN.cpu().numpy().astype(np.float64), dphi0.cpu().numpy().astype(np.float64), dD,
+           None if da is None else da.cpu().numpy().astype(np.float64))
+    s.close()
+    return out
+
+
+def oracle_grads(O, case, phi0, a, sched, g):
+    p = oracle_params(O, case)
+    uf = case.u_of_t(a, sched)
+    gp, gD, du, _ = O.adjoint_gradients(p, phi0.astype(np.float64).reshape(-1), case.steps,
+                                        g.reshape(-1), u_of_t=uf)
+    da = None
+    if a is not None:
+        s = np.ones((case.steps, case.dim)) if sched is None else \
+            sched.astype(np.float64)[np.arange(case.steps) % len(sched)]
+        da = np.einsum("td,tdc->dc", s, du).reshape((case.dim,) + case.shape)
+    return gp.reshape(case.shape), gD, da
+
+
+CASES = [
+    Case(nx=70, ny=40, steps=60),
+    Case(nx=70, ny=40, steps=60, sched=False),
+    Case(nx=70, ny=41, steps=60, bc=("noflux", "noflux")),
+    Case(nx=70, ny=41, steps=60, bc=("bounceback", "bounceback")),
+    Case(nx=64, ny=33, steps=60, bc=("noflux", "noflux"), ukind="row"),
+    Case(nx=64, ny=32, steps=40, ukind="none", sched=False),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c.bc[0]}-{c.ukind}-{'sched' if c.sched else 'const'}")
+def test_adjoint_matches_fp64_oracle_adjoint(O, case):
+    phi0, a, sched = case.inputs()
+    g = np.random.default_rng(5).standard_normal(case.shape)
+    a_grad = a if case.ukind == "field" else None
+    phiN, dphi0, dD, da = gpu_grads(case, phi0, a, sched, g) if case.ukind == "field" else \
+        _gpu_nofield(case, phi0, a, sched, g)
+    wp, wD, wa = oracle_grads(O, case, phi0, a, sched, g)
+    assert rel_l2(dphi0, wp) < 1e-5
+    assert np.abs(dD - wD).max() <= 1e-4 * np.abs(wD).max()
+    if a_grad is not None:
+        assert rel_l2(da, wa) < 1e-4
+
+
+def _gpu_nofield(case, phi0, a, sched, g):
+    s = Solver(nx=case.nx, ny=case.ny, bc=case.bc)
+    s.set_D(case.D)
+    if a is not None:
+        s.set_velocity(torch.from_numpy(a).cuda(), None if sched is None else torch.from_numpy(sched).cuda(),
+                       kind="row")
+    phiN = s.forward_ckpt(torch.from_numpy(phi0).cuda(), case.steps)
+    dphi0, dD, ds, _ = s.backward(torch.from_numpy(g.astype(np.float32)).cuda())
+    s.close()
+    return phiN.cpu().numpy(), dphi0.cpu().numpy().astype(np.float64), dD, None
+
+
+def test_gradient_D_against_central_differences(O):
+    """dL/dD from the GPU adjoint vs FP64 central differences of the oracle
+    (the symmetric parametrisation: D01 and D10 move together)."""
+    case = Case(nx=60, ny=44, steps=80)
+    phi0, a, sched = case.inputs()
+    g = np.random.default_rng(8).standard_normal(case.shape)
+    _, _, dD, _ = gpu_grads(case, phi0, a, sched, g)
+    uf = case.u_of_t(a, sched)
+    h = 1e-6
+    for (i, j) in ((0, 0), (0, 1), (1, 1)):
+        vals = []
+        for sgn in (1, -1):
+            D = case.D.copy()
+            D[i, j] += sgn * h
+            if i != j:
+                D[j, i] += sgn * h
+            p = oracle_params(O, Case(nx=case.nx, ny=case.ny, D=D))
+            phi = O.run(p, phi0.astype(np.float64).reshape(-1), case.steps, u_of_t=uf)
+            vals.append(float((g.reshape(-1) * phi).sum()))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        an = dD[i, j] + (dD[j, i] if i != j else 0.0)
+        assert abs(an - fd) <= 1e-4 * abs(fd), (i, j, an, fd)
+
+
+def test_checkpoint_interval_does_not_change_gradients():
+    case = Case(nx=50, ny=30, steps=45)
+    phi0, a, sched = case.inputs()
+    g = np.random.default_rng(2).standard_normal(case.shape)
+    ref = gpu_grads(case, phi0, a, sched, g, every=1)
+    for every in (0, 7, 45, 100):
+        got = gpu_grads(case, phi0, a, sched, g, every=every)
+        assert np.array_equal(got[1], ref[1])
+        assert np.array_equal(got[2], ref[2])
+        assert np.array_equal(got[3], ref[3])
+
+
+def test_forward_ckpt_equals_plain_forward():
+    from _common import run_gpu
+
+    case = Case(nx=80, ny=36, steps=33)
+    phi0, a, sched = case.inputs()
+    ref, _ = run_gpu(case, phi0, a, sched)
+    got = gpu_grads(case, phi0, a, sched, np.zeros(case.shape))[0]
+    assert np.array_equal(got, ref)
+
+
+def test_autograd_function_and_loss_backward():
+    from paper_1404_2363_gb300.autograd import lbm_run
+
+    case = Case(nx=48, ny=40, steps=30)
+    phi0, a, sched = case.inputs()
+    s = Solver(nx=case.nx, ny=case.ny)
+    p0 = torch.from_numpy(phi0).cuda().requires_grad_(True)
+    D = torch.tensor(case.D, dtype=torch.float64, requires_grad=True)
+    at = torch.from_numpy(a).cuda().requires_grad_(True)
+    st = torch.from_numpy(sched).cuda()
+    obs = torch.rand(case.shape, device="cuda")
+    phiN = lbm_run(p0, D, at, solver=s, nsteps=case.steps, sched=st)
+    loss = 0.5 * ((phiN - obs) ** 2).sum()
+    loss.backward()
+    g = (phiN - obs).detach().cpu().numpy().astype(np.float64)
+    ref = gpu_grads(case, phi0, a, sched, g)
+    assert torch.allclose(p0.grad.cpu().double(), torch.from_numpy(ref[1]), rtol=1e-5, atol=1e-6)
+    assert np.allclose(D.grad.numpy(), ref[2], rtol=1e-5, atol=1e-8)
+    assert torch.allclose(at.grad.cpu().double(), torch.from_numpy(ref[3]), rtol=1e-4, atol=1e-6)
+
+
+def test_inverse_problem_recovers_D():
+    """Reduced form of the inverse-problem workload: recover the three entries of
+    D from a final snapshot with L-BFGS through the adjoint."""
+    from paper_1404_2363_gb300 import workloads as W
+    from paper_1404_2363_gb300.autograd import lbm_run
+
+    n, steps = 128, 300
+    g = W.rng(5)
+    u = W.stream_function_velocity(n, g)
+    phi0 = (1.0 + W.fourier_field(n, g, modes=16)).astype(np.float32)
+    D_true = W.D_ANISO
+    s = Solver(nx=n, ny=n)
+    a = torch.from_numpy(u.astype(np.float32)).cuda()
+    p0 = torch.from_numpy(phi0).cuda()
+    with torch.no_grad():
+        obs = lbm_run(p0, torch.tensor(D_true), a, solver=s, nsteps=steps).clone()
+    # D = L L^T with a positive diagonal keeps every trial point SPD
+    theta = torch.tensor([np.log(np.sqrt(0.03)), 0.0, np.log(np.sqrt(0.03))], dtype=torch.float64,
+                         requires_grad=True)
+
+    def D_of(th):
+        l00, l10, l11 = torch.exp(th[0]), th[1], torch.exp(th[2])
+        return torch.stack([torch.stack([l00 * l00, l00 * l10]),
+                            torch.stack([l00 * l10, l10 * l10 + l11 * l11])])
+
+    opt = torch.optim.LBFGS([theta], lr=1.0, max_iter=40, line_search_fn="strong_wolfe")
+
+    def closure():
+        opt.zero_grad()
+        phiN = lbm_run(p0, D_of(theta), a, solver=s, nsteps=steps)
+        loss = ((phiN - obs) ** 2).sum() * 1e3
+        loss.backward()
+        return loss
+
+    for _ in range(3):
+        opt.step(closure)
+    est = D_of(theta).detach().numpy()
+    assert np.allclose(est, D_true, rtol=2e-3, atol=2e-5), est
