@@ -333,6 +333,42 @@ def e2e_run(store: str, steps: int):
             "note": f"one lbm_cde_run_host call of {steps} steps; per-step bytes are the call's copies / steps"}
 
 
+def batch_bench(steps: int):
+    """The Taylor-Aris batch workload: 64 uneven channels in one launch per graph
+    chunk, moments every step; mode and tile width from the autotuner."""
+    import torch
+
+    from paper_1404_2363_gb300 import workloads as W
+    from paper_1404_2363_gb300.batch import Batch, mean_velocity, poiseuille_row
+
+    chans = W.taylor_aris_batch(64)
+    descs, phis = [], []
+    for c in chans:
+        u = poiseuille_row(c.ny, c.U)
+        descs.append({"nx": c.nx, "ny": c.ny, "D": np.eye(2) * c.alpha, "u_row": u,
+                      "s": [1.0, 1.1, 1.1, None, 1 / c.tau, None, 1 / c.tau, 1.2, 1.2], "tie": False,
+                      "x_ref0": 0.2 * c.nx, "x_ref_velocity": mean_velocity(u)})
+        phis.append(c.phi0().astype(np.float32))
+    b = Batch(descs, graph_steps=64)
+    b.set_phi(phis)
+    mode, tile = b.autotune(steps=128)
+    b.set_phi(phis)
+    n = max(64, (min(steps, 2000) // 64) * 64)
+    b.run(64, moments=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run(n, moments=True)
+    dt = time.perf_counter() - t0
+    cells = b.ncat
+    b.close()
+    peak, kind = peaks()
+    gbs = cells * 72 / (dt / n) / 1e9
+    return {"instances": len(chans), "cells": cells, "steps": n, "MLUPS": cells * n / dt / 1e6,
+            "bytes_per_lu": 72, "achieved_gbs": gbs, f"frac_of_{kind}_hbm": gbs / peak,
+            "mode": mode, "tile_cols": tile,
+            "timing": "host wall clock around lbm_cde_batch_run (graph replays + per-step moment copies)"}
+
+
 def adjoint_cost(store: str, ms_forward: float, nsteps: int = 400):
     """Cost of the reverse sweep (checkpoint-segment recompute + adjoint kernels,
     sqrt(N) checkpoints) per step, against one plain forward step: once for the
@@ -417,6 +453,8 @@ def main():
                         "achieved_gbs": av, "frac_of_" + peak_kind + "_hbm": av / peak}
     torch.cuda.empty_cache()
 
+    variants["taylor_aris_batch"] = batch_bench(args.steps)
+    torch.cuda.empty_cache()
     adjoint = adjoint_cost(store, ms_forward=dt / args.steps * 1e3)
     e2e = e2e_run(store, args.steps)
     if rank != 0:

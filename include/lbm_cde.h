@@ -239,6 +239,75 @@ lbm_status lbm_cde_forward_ckpt(lbm_cde_t h, const float* phi0_dev, int64_t nste
 lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dphi0_dev, double* dL_dD_host,
                             double* dL_ds_host, float* dL_da_dev);
 
+/* ---- Batched channels (Sec. 3.2 set-up, many instances per launch) --------
+ * Independent D2Q9 MRT-A instances of uneven size, each with its own D, rates,
+ * walls and row velocity profile u(y), advanced together; every step also
+ * reduces, per instance, the moments of the cross-section mean
+ *     phi-bar(x) = sum_y w_y phi(x, y)   (w = 1/2 on the two wall nodes, 1 else;
+ *                                          w = 1 everywhere for periodic y)
+ * as M_k = sum_x phi-bar(x) xi^k, k = 0, 1, 2, with xi = x - c(t) wrapped to
+ * [-nx/2, nx/2) and c(t) = round(x_ref0 + x_ref_velocity * t): the sums of
+ * Eq. 47, from which sigma^2 = M2/M0 - (M1/M0)^2 and alpha_L (Eq. 46). */
+typedef struct lbm_cde_batch_s* lbm_cde_batch_t;
+
+enum { LBM_BATCH_AUTO = 0, LBM_BATCH_PERSISTENT = 1, LBM_BATCH_PER_STEP = 2 };
+
+typedef struct {
+    int64_t nx, ny;          /* nx periodic columns, ny nodes across (walls on nodes 0, ny-1) */
+    int32_t bc_lo_y, bc_hi_y;/* LBM_BC_NOFLUX_NODE, LBM_BC_BOUNCEBACK or LBM_BC_PERIODIC (both) */
+    double D[4];             /* diffusion tensor, row-major 2 x 2, symmetric positive definite;
+                                A = (3 D + I/2)^-1 (Eq. 36, MRT-A factor 1/3) */
+    double s[15];            /* diagonal rates (NaN: s0 = 1, s1 = s2 = 1.1, s7 = s8 = 1.2) */
+    int32_t tie_q_rates;     /* 1: s4 = sxx, s6 = syy */
+    const float* u_row_dev;  /* device [2][ny] velocity per row (borrowed), or NULL (u = 0) */
+    double x_ref0;           /* moment reference centre at t = 0 (node index) */
+    double x_ref_velocity;   /* its drift per step */
+} lbm_cde_channel_desc;
+
+typedef struct {
+    int32_t mode;            /* LBM_BATCH_AUTO (persistent until autotuned) / PERSISTENT / PER_STEP */
+    int32_t tile_cols;       /* columns per tile: 128, 256 or 512 */
+    int32_t graph_steps;     /* steps per captured CUDA graph (ring of moments), 1 .. 4096 */
+    int64_t barrier_timeout_cycles; /* clock64 cycles a CTA waits at a grid barrier before the
+                                launch gives up with LBM_E_TIMEOUT (default 2e9, about 1 s) */
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free_)(void* ptr, void* ctx);
+    void* alloc_ctx;
+    void* stream;
+} lbm_cde_batch_opts;
+
+lbm_status lbm_cde_batch_opts_init(lbm_cde_batch_opts* opts);
+
+/* Creates a batch of n instances. Cells of all instances are concatenated in
+ * instance order (x fastest, then y). Errors: LBM_E_ARG, LBM_E_NOT_SPD, LBM_E_OOM. */
+lbm_status lbm_cde_batch_create(const lbm_cde_channel_desc* descs, int32_t n, const lbm_cde_batch_opts* opts,
+                                lbm_cde_batch_t* out);
+lbm_status lbm_cde_batch_destroy(lbm_cde_batch_t b);
+
+/* Total number of cells of all instances. */
+lbm_status lbm_cde_batch_cells(lbm_cde_batch_t b, int64_t* ncat);
+
+/* f = f^eq(phi0, u) from a device FP32 field [ncat] (concatenated), step 0. */
+lbm_status lbm_cde_batch_set_phi(lbm_cde_batch_t b, const float* phi_dev);
+
+/* phi of the current state into a device FP32 buffer [ncat]. */
+lbm_status lbm_cde_batch_get_phi(lbm_cde_batch_t b, float* phi_dev);
+
+/* Runs nsteps steps (full chunks replay one captured CUDA graph) and copies the
+ * moments of every step to moments_host ([nsteps][n][3] doubles, or NULL).
+ * Synchronising; returns LBM_E_TIMEOUT if a grid barrier gave up (the state is
+ * then invalid until the next set_phi). */
+lbm_status lbm_cde_batch_run(lbm_cde_batch_t b, int64_t nsteps, double* moments_host);
+
+/* Times every execution mode x tile width on `steps` steps, keeps the fastest
+ * (restoring the state and step count) and reports it. */
+lbm_status lbm_cde_batch_autotune(lbm_cde_batch_t b, int64_t steps, int32_t* mode_out, int32_t* tile_out);
+
+/* Selects an execution mode and tile width explicitly. */
+lbm_status lbm_cde_batch_config(lbm_cde_batch_t b, int32_t mode, int32_t tile_cols);
+
+const char* lbm_cde_batch_last_error(lbm_cde_batch_t b);
+
 /* Allocation-free FP64 sum of phi over a raw state (no counterpart in the
  * paper; an addition for callers that cannot allocate device memory, such as
  * code running while a stream is captured into a CUDA graph or under a fixed

@@ -47,6 +47,37 @@ class LbmDesc(ctypes.Structure):
     ]
 
 
+LBM_BATCH_AUTO, LBM_BATCH_PERSISTENT, LBM_BATCH_PER_STEP = 0, 1, 2
+
+
+class ChannelDesc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int64),
+        ("ny", ctypes.c_int64),
+        ("bc_lo_y", ctypes.c_int32),
+        ("bc_hi_y", ctypes.c_int32),
+        ("D", ctypes.c_double * 4),
+        ("s", ctypes.c_double * 15),
+        ("tie_q_rates", ctypes.c_int32),
+        ("u_row_dev", ctypes.c_void_p),
+        ("x_ref0", ctypes.c_double),
+        ("x_ref_velocity", ctypes.c_double),
+    ]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int32),
+        ("tile_cols", ctypes.c_int32),
+        ("graph_steps", ctypes.c_int32),
+        ("barrier_timeout_cycles", ctypes.c_int64),
+        ("alloc", ALLOC_FN),
+        ("free_", FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
 class LbmError(RuntimeError):
     def __init__(self, status: int, what: str, msg: str):
         self.status = status
@@ -85,6 +116,17 @@ SIGNATURES = {
     "lbm_cde_grad_rates": [_P, _DP, _DP, _DP],
     "lbm_cde_forward_ckpt": [_P, _P, _I64, _I64, _P],
     "lbm_cde_backward": [_P, _P, _P, _DP, _DP, _P],
+    "lbm_cde_batch_opts_init": [ctypes.POINTER(BatchOpts)],
+    "lbm_cde_batch_create": [ctypes.POINTER(ChannelDesc), ctypes.c_int32, ctypes.POINTER(BatchOpts),
+                             ctypes.POINTER(_P)],
+    "lbm_cde_batch_destroy": [_P],
+    "lbm_cde_batch_cells": [_P, ctypes.POINTER(_I64)],
+    "lbm_cde_batch_set_phi": [_P, _P],
+    "lbm_cde_batch_get_phi": [_P, _P],
+    "lbm_cde_batch_run": [_P, _I64, _DP],
+    "lbm_cde_batch_autotune": [_P, _I64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
+    "lbm_cde_batch_config": [_P, ctypes.c_int32, ctypes.c_int32],
+    "lbm_cde_batch_last_error": [_P],
     "lbm_cde_sum_state_noalloc": [_P, ctypes.c_int32, ctypes.c_int32, _I64, _P, _P],
     "lbm_cde_noalloc_last_error": [],
 }

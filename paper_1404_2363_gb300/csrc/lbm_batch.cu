@@ -1,0 +1,784 @@
+// Batched channels: many independent D2Q9 instances (uneven nx x ny, own D,
+// rates and row velocity profile) advanced together, with the moments of the
+// cross-section mean (Sec. 3.2, Eq. 46-47) reduced every step.
+//
+// Work unit ("tile"): one instance and a run of TW consecutive columns; a CTA
+// of TW threads walks all ny rows of its columns (walls at the two ends of
+// the walk), so the cross-section sum phi-bar(x) = sum_y w_y phi(x, y)
+// (trapezoid weights, walls on the nodes) stays in a register. Per tile the
+// partial moments sum phi-bar {1, xi, xi^2} go to a fixed slot (xi = x minus
+// an integer reference centre, wrapped to [-nx/2, nx/2)), and a fixed-order
+// pass sums them per instance, so the moments are deterministic.
+//
+// Two execution modes, chosen by the autotuner:
+//   PERSISTENT : one cooperative launch runs K steps; CTAs take tiles from an
+//                atomic counter, and a grid barrier (bounded spin, then
+//                LBM_E_TIMEOUT) separates the steps;
+//   PER_STEP   : one launch per step plus one moment-reduction launch.
+// Either is captured once into a CUDA graph of K steps and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm_cde.h"
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+struct InstDev {
+    int nx, ny;
+    long long off;        // first cell of this instance in the concatenated cell index
+    int bc_lo, bc_hi;
+    long long tile0, ntiles;
+    long long xref0;      // moment reference centre at step 0 (integer node)
+    double vref;          // reference drift per step
+    const float* urow;    // [2][ny] or nullptr
+    Coef c;
+};
+
+struct TileDev {
+    int inst;
+    int x0;
+};
+
+struct BatchArgs {
+    const InstDev* inst;
+    const TileDev* tiles;
+    long long ntiles;
+    int ninst;
+    long long ncat;           // total cells
+    float* buf[2];            // state planes [9][ncat], ping-pong
+    double* partials;         // [2][ntiles][3]
+    double* moments;          // ring [ring][ninst][3], slot (k - 1) mod ring
+    int ring;
+    const long long* kdev;    // last completed step t: this launch computes t+1 .. t+nsteps
+    int nsteps;               // steps in this launch
+    unsigned* counter;        // [2] tile counters (PERSISTENT)
+    unsigned* bar_count;
+    unsigned* bar_gen;
+    int* status;              // device status word (LBM_E_TIMEOUT on a barrier time-out)
+    long long spin_limit;     // clock64 cycles a CTA may wait at a barrier
+};
+
+__device__ __forceinline__ long long wrap_ll(long long v, long long n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// One tile of one step: pull-stream, walls, collide, store; returns the tile's
+// partial moments in red (thread 0).
+template <int TW>
+__device__ void batch_tile(const BatchArgs& a, long long t, long long k, const float* __restrict__ src,
+                           float* __restrict__ dst, Coef& cs, double* red3)
+{
+    const TileDev td = a.tiles[t];
+    const InstDev& I = a.inst[td.inst];
+    __syncthreads();
+    if (threadIdx.x == 0) cs = I.c;
+    __syncthreads();
+    const int nx = I.nx, ny = I.ny;
+    const long long N = a.ncat;
+    const int x = td.x0 + threadIdx.x;
+    const bool live = x < nx;
+    const int xc = live ? x : nx - 1;
+    const int xs[3] = {xc + 1 == nx ? 0 : xc + 1, xc, xc == 0 ? nx - 1 : xc - 1};
+    const long long base = I.off;
+    float col = 0.f, comp = 0.f;   // Kahan sum of w_y phi over the column
+    for (int y = 0; y < ny; ++y) {
+        const int ys[3] = {y + 1 == ny ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};
+        float f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            f[i] = __ldg(src + (long long)i * N + base + (long long)ys[D2Q9::ey(i) + 1] * nx + xs[D2Q9::ex(i) + 1]);
+        const bool lo = y == 0 && I.bc_lo != BC_PERIODIC;
+        const bool hi = y == ny - 1 && I.bc_hi != BC_PERIODIC;
+        if (lo || hi) {
+            const int kind = lo ? I.bc_lo : I.bc_hi;
+            const long long cell = base + (long long)y * nx + xc;
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                if (D2Q9::ey(i) != 0 && ((D2Q9::ey(i) == 1) == lo)) {
+                    if (kind == BC_BOUNCE) f[i] = __ldg(src + (long long)opposite<D2Q9>(i) * N + cell);
+                    else f[i] = f[mirror_y<D2Q9>(i)];
+                }
+        }
+        float ux = 0.f, uy = 0.f;
+        if (I.urow) {
+            ux = __ldg(I.urow + y);
+            uy = __ldg(I.urow + ny + y);
+        }
+        float phi = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) phi += f[i];
+        collide<D2Q9>(f, ux, uy, 0.f, cs);
+        if (live) {
+            const long long cell = base + (long long)y * nx + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) dst[(long long)i * N + cell] = f[i];
+        }
+        const float w = (I.bc_lo != BC_PERIODIC && (y == 0 || y == ny - 1)) ? 0.5f : 1.0f;
+        const float yv = w * phi - comp;
+        const float tv = col + yv;
+        comp = (tv - col) - yv;
+        col = tv;
+    }
+    // moments of phi-bar about the integer reference centre
+    const long long cref = I.xref0 + (long long)llround(I.vref * (double)k);
+    long long xi = wrap_ll((long long)x - cref, nx);
+    if (xi >= (nx + 1) / 2) xi -= nx;
+    const double pb = live ? (double)col : 0.0;
+    double m0 = pb, m1 = pb * (double)xi, m2 = pb * (double)xi * (double)xi;
+    // block sum: warp shuffles then shared memory, fixed order
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        m0 += __shfl_down_sync(0xffffffffu, m0, off);
+        m1 += __shfl_down_sync(0xffffffffu, m1, off);
+        m2 += __shfl_down_sync(0xffffffffu, m2, off);
+    }
+    __shared__ double wred[TW / 32][3];
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        wred[warp][0] = m0;
+        wred[warp][1] = m1;
+        wred[warp][2] = m2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0, s1 = 0, s2 = 0;
+        for (int w = 0; w < TW / 32; ++w) {
+            s0 += wred[w][0];
+            s1 += wred[w][1];
+            s2 += wred[w][2];
+        }
+        red3[0] = s0;
+        red3[1] = s1;
+        red3[2] = s2;
+    }
+}
+
+__device__ void reduce_instance(const BatchArgs& a, int i, const double* part, double* out)
+{
+    const InstDev& I = a.inst[i];
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (long long t = I.tile0; t < I.tile0 + I.ntiles; ++t) {
+        s0 += part[t * 3 + 0];
+        s1 += part[t * 3 + 1];
+        s2 += part[t * 3 + 2];
+    }
+    out[0] = s0;
+    out[1] = s1;
+    out[2] = s2;
+}
+
+// Grid barrier with a bounded wait: returns false (and latches LBM_E_TIMEOUT)
+// if the other CTAs do not arrive within spin_limit cycles.
+__device__ bool grid_barrier(const BatchArgs& a)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned* gen = a.bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(a.bar_count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            *a.bar_count = 0u;
+            __threadfence();
+            atomicAdd(a.bar_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (clock64() - t0 > a.spin_limit || *((volatile int*)a.status) != 0) {
+                    atomicCAS(a.status, 0, (int)LBM_E_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ double* moment_slot(const BatchArgs& a, long long k, int i)
+{
+    return a.moments + (((k - 1) % a.ring) * a.ninst + i) * 3;
+}
+
+// B_0 sits in buf[0], so B_{k-1} is in buf[(k-1) & 1] and B_k goes to buf[k & 1].
+template <int TW>
+__global__ void __launch_bounds__(TW) k_batch_persistent(const BatchArgs a)
+{
+    __shared__ Coef cs;
+    __shared__ double red3[3];
+    __shared__ long long tile_s;
+    const long long t0 = *a.kdev;
+    for (int s = 0; s < a.nsteps; ++s) {
+        const long long k = t0 + 1 + s;
+        const float* src = a.buf[(k - 1) & 1];
+        float* dst = a.buf[k & 1];
+        double* part = a.partials + (long long)(k & 1) * a.ntiles * 3;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.counter[(k + 1) & 1] = 0u;
+        while (true) {
+            __syncthreads();
+            if (threadIdx.x == 0) tile_s = (long long)atomicAdd(a.counter + (k & 1), 1u);
+            __syncthreads();
+            const long long t = tile_s;
+            if (t >= a.ntiles) break;
+            batch_tile<TW>(a, t, k, src, dst, cs, red3);
+            if (threadIdx.x == 0) {
+                part[t * 3 + 0] = red3[0];
+                part[t * 3 + 1] = red3[1];
+                part[t * 3 + 2] = red3[2];
+            }
+        }
+        if (!grid_barrier(a)) return;
+        // moments of step k, one thread per instance
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.ninst; i += gridDim.x * blockDim.x)
+            reduce_instance(a, i, part, moment_slot(a, k, i));
+    }
+}
+
+template <int TW>
+__global__ void __launch_bounds__(TW) k_batch_step(const BatchArgs a)
+{
+    __shared__ Coef cs;
+    __shared__ double red3[3];
+    const long long k = *a.kdev + 1;
+    const float* src = a.buf[(k - 1) & 1];
+    float* dst = a.buf[k & 1];
+    const long long t = blockIdx.x;
+    batch_tile<TW>(a, t, k, src, dst, cs, red3);
+    if (threadIdx.x == 0) {
+        double* part = a.partials + (long long)(k & 1) * a.ntiles * 3;
+        part[t * 3 + 0] = red3[0];
+        part[t * 3 + 1] = red3[1];
+        part[t * 3 + 2] = red3[2];
+    }
+}
+
+__global__ void k_batch_moments(const BatchArgs a)
+{
+    const long long k = *a.kdev + 1;
+    const double* part = a.partials + (long long)(k & 1) * a.ntiles * 3;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.ninst; i += gridDim.x * blockDim.x)
+        reduce_instance(a, i, part, moment_slot(a, k, i));
+}
+
+__global__ void k_batch_advance(long long* kdev, int n)
+{
+    *kdev += n;
+}
+
+__global__ void k_batch_init(const InstDev* __restrict__ inst, int ninst, const float* __restrict__ phi0,
+                             float* __restrict__ f, long long ncat)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncat;
+         c += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = ninst - 1;          // instance holding cell c (offsets ascend)
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (inst[mid].off <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const InstDev& I = inst[lo];
+        const int y = (int)((c - I.off) / I.nx);
+        const float ux = I.urow ? I.urow[y] : 0.f, uy = I.urow ? I.urow[I.ny + y] : 0.f;
+        const float p = phi0[c];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[(long long)i * ncat + c] = p * feq_unit<D2Q9>(I.c, i, ux, uy, 0.f);
+    }
+}
+
+__global__ void k_batch_phi(const float* __restrict__ f, long long ncat, float* __restrict__ out)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncat;
+         c += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) s += f[(long long)i * ncat + c];
+        out[c] = s;
+    }
+}
+
+template <int TW>
+static cudaError_t launch_mode(int mode, const BatchArgs& a, int grid_persistent, long long* kdev,
+                               cudaStream_t st)
+{
+    if (mode == LBM_BATCH_PERSISTENT) {
+        // tile counters start at zero for the first step of the launch
+        cudaError_t e = cudaMemsetAsync(a.counter, 0, 2 * sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+        void* args[] = {(void*)&a};
+        e = cudaLaunchCooperativeKernel((const void*)k_batch_persistent<TW>, dim3(grid_persistent),
+                                                    dim3(TW), args, 0, st);
+        if (e != cudaSuccess) return e;
+        k_batch_advance<<<1, 1, 0, st>>>(kdev, a.nsteps);
+        return cudaGetLastError();
+    }
+    for (int s = 0; s < a.nsteps; ++s) {
+        k_batch_step<TW><<<(unsigned)a.ntiles, TW, 0, st>>>(a);
+        k_batch_moments<<<(a.ninst + 127) / 128, 128, 0, st>>>(a);
+        k_batch_advance<<<1, 1, 0, st>>>(kdev, 1);
+    }
+    return cudaGetLastError();
+}
+
+template <int TW>
+static int persistent_grid()
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_persistent<TW>, TW, 0);
+    return std::max(1, per) * sms;
+}
+
+}  // namespace lbm
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct lbm_cde_batch_s {
+    lbm_cde_batch_opts o{};
+    int n = 0;
+    std::vector<lbm::InstDev> inst;
+    std::vector<lbm::TileDev> tiles;
+    long long ncat = 0;
+    lbm::InstDev* inst_dev = nullptr;
+    lbm::TileDev* tiles_dev = nullptr;
+    float* buf[2] = {nullptr, nullptr};
+    double* partials = nullptr;
+    double* moments = nullptr;     // ring [chunk][n][3]
+    unsigned* sync = nullptr;      // counter[2], bar_count, bar_gen, status, step index (long long)
+    int* status = nullptr;
+    long long* kdev = nullptr;
+    long long t = 0;
+    bool ready = false;
+    int mode = LBM_BATCH_PERSISTENT;
+    int tw = 256;
+    int chunk = 64;                // steps per graph replay
+    cudaGraphExec_t graph = nullptr;   // one chunk of steps, built lazily for (mode, tw)
+    int graph_key[2] = {-1, -1};
+    bool use_graph = true;
+    cudaStream_t st = nullptr;
+    std::string err;
+};
+
+static thread_local std::string g_batch_err;
+
+static lbm_status bfail(lbm_cde_batch_t b, lbm_status s, const std::string& m)
+{
+    if (b) b->err = m;
+    else g_batch_err = m;
+    return s;
+}
+
+#define BCK(b, call)                                                                       \
+    do {                                                                                   \
+        cudaError_t _e = (call);                                                           \
+        if (_e != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+static void* balloc(lbm_cde_batch_t b, size_t n)
+{
+    if (b->o.alloc) return b->o.alloc(n ? n : 16, b->o.alloc_ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, n ? n : 16) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void bfree(lbm_cde_batch_t b, void* p)
+{
+    if (!p) return;
+    if (b->o.free_) b->o.free_(p, b->o.alloc_ctx);
+    else if (!b->o.alloc) cudaFree(p);
+}
+
+static void batch_coef(const lbm_cde_channel_desc& d, const double A[4], lbm::Coef& c)
+{
+    const double defaults[9] = {1.0, 1.1, 1.1, 0, 1.0, 0, 1.0, 1.2, 1.2};
+    double s[15] = {0};
+    for (int k = 0; k < 9; ++k) s[k] = std::isnan(d.s[k]) ? defaults[k] : d.s[k];
+    if (d.tie_q_rates) {
+        s[4] = A[0];
+        s[6] = A[3];
+    }
+    std::memset(&c, 0, sizeof(c));
+    for (int k = 0; k < 15; ++k) c.s[k] = (float)s[k];
+    for (int a = 0; a < 2; ++a)
+        for (int bb = 0; bb < 2; ++bb) {
+            c.A[a * 2 + bb] = (float)A[a * 2 + bb];
+            c.C[a * 2 + bb] = (float)((A[a * 2 + bb] / 2.0 - (a == bb ? 1.0 : 0.0)) * s[4 + 2 * bb]);
+        }
+    // MRT-A equilibrium, alpha1 = -8, alpha2 = 8 (Eq. 37), f^eq of Eq. 17
+    c.meq1 = -2.f;
+    c.meq2 = 2.f;
+    c.w0 = (float)(20.0 / 36.0);
+    c.wa = (float)(8.0 / 144.0);
+    c.wd = (float)(8.0 / 144.0);
+    c.ka = (float)(48.0 / 144.0);
+    c.kd = (float)(12.0 / 144.0);
+}
+
+static lbm::BatchArgs batch_args(lbm_cde_batch_t b, int nsteps)
+{
+    lbm::BatchArgs a{};
+    a.inst = b->inst_dev;
+    a.tiles = b->tiles_dev;
+    a.ntiles = (long long)b->tiles.size();
+    a.ninst = b->n;
+    a.ncat = b->ncat;
+    a.buf[0] = b->buf[0];
+    a.buf[1] = b->buf[1];
+    a.partials = b->partials;
+    a.moments = b->moments;
+    a.ring = b->chunk;
+    a.kdev = b->kdev;
+    a.nsteps = nsteps;
+    a.counter = b->sync;
+    a.bar_count = b->sync + 2;
+    a.bar_gen = b->sync + 3;
+    a.status = b->status;
+    a.spin_limit = b->o.barrier_timeout_cycles;
+    return a;
+}
+
+static cudaError_t launch_batch(lbm_cde_batch_t b, const lbm::BatchArgs& a)
+{
+    switch (b->tw) {
+        case 128: return lbm::launch_mode<128>(b->mode, a, lbm::persistent_grid<128>(), b->kdev, b->st);
+        case 512: return lbm::launch_mode<512>(b->mode, a, lbm::persistent_grid<512>(), b->kdev, b->st);
+        default: return lbm::launch_mode<256>(b->mode, a, lbm::persistent_grid<256>(), b->kdev, b->st);
+    }
+}
+
+static void drop_graph(lbm_cde_batch_t b)
+{
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->graph_key[0] = b->graph_key[1] = -1;
+}
+
+// Captures one chunk of steps into a graph. The step index and the buffer
+// parity live on the device, so the same graph serves every chunk.
+static lbm_status ensure_graph(lbm_cde_batch_t b)
+{
+    if (b->graph && b->graph_key[0] == b->mode && b->graph_key[1] == b->tw) return LBM_OK;
+    drop_graph(b);
+    cudaStream_t cap = nullptr;
+    BCK(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaStream_t keep = b->st;
+        b->st = cap;
+        lbm::BatchArgs a = batch_args(b, b->chunk);
+        cudaError_t le = launch_batch(b, a);
+        b->st = keep;
+        e = cudaStreamEndCapture(cap, &g);
+        if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->graph = nullptr;
+        b->use_graph = false;     // run chunks with direct launches instead
+        return LBM_OK;
+    }
+    b->graph_key[0] = b->mode;
+    b->graph_key[1] = b->tw;
+    return LBM_OK;
+}
+
+static lbm_status rebuild_tiles(lbm_cde_batch_t b)
+{
+    b->tiles.clear();
+    for (int i = 0; i < b->n; ++i) {
+        b->inst[i].tile0 = (long long)b->tiles.size();
+        for (int x0 = 0; x0 < b->inst[i].nx; x0 += b->tw) b->tiles.push_back({i, x0});
+        b->inst[i].ntiles = (long long)b->tiles.size() - b->inst[i].tile0;
+    }
+    bfree(b, b->tiles_dev);
+    bfree(b, b->partials);
+    b->tiles_dev = static_cast<lbm::TileDev*>(balloc(b, sizeof(lbm::TileDev) * b->tiles.size()));
+    b->partials = static_cast<double*>(balloc(b, sizeof(double) * 6 * b->tiles.size()));
+    if (!b->tiles_dev || !b->partials) return bfail(b, LBM_E_OOM, "tile allocation failed");
+    BCK(b, cudaMemcpyAsync(b->tiles_dev, b->tiles.data(), sizeof(lbm::TileDev) * b->tiles.size(),
+                           cudaMemcpyHostToDevice, b->st));
+    BCK(b, cudaMemcpyAsync(b->inst_dev, b->inst.data(), sizeof(lbm::InstDev) * b->n, cudaMemcpyHostToDevice,
+                           b->st));
+    BCK(b, cudaStreamSynchronize(b->st));
+    drop_graph(b);
+    return LBM_OK;
+}
+
+extern "C" {
+
+lbm_status lbm_cde_batch_opts_init(lbm_cde_batch_opts* o)
+{
+    if (!o) return bfail(nullptr, LBM_E_ARG, "NULL opts");
+    std::memset(o, 0, sizeof(*o));
+    o->mode = LBM_BATCH_AUTO;
+    o->tile_cols = 256;
+    o->graph_steps = 64;
+    o->barrier_timeout_cycles = 2000000000LL;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_batch_create(const lbm_cde_channel_desc* descs, int32_t n, const lbm_cde_batch_opts* opts,
+                                lbm_cde_batch_t* out)
+{
+    if (!descs || n < 1 || !out) return bfail(nullptr, LBM_E_ARG, "bad argument");
+    *out = nullptr;
+    lbm_cde_batch_opts o;
+    if (opts) o = *opts;
+    else lbm_cde_batch_opts_init(&o);
+    if ((o.alloc == nullptr) != (o.free_ == nullptr)) return bfail(nullptr, LBM_E_ARG, "alloc/free_ mismatch");
+    if (o.tile_cols != 128 && o.tile_cols != 256 && o.tile_cols != 512)
+        return bfail(nullptr, LBM_E_ARG, "tile_cols must be 128, 256 or 512");
+    if (o.graph_steps < 1 || o.graph_steps > 4096) return bfail(nullptr, LBM_E_ARG, "graph_steps in [1, 4096]");
+    if (o.barrier_timeout_cycles < 0) return bfail(nullptr, LBM_E_ARG, "negative barrier timeout");
+    lbm_cde_batch_t b = new (std::nothrow) lbm_cde_batch_s();
+    if (!b) return bfail(nullptr, LBM_E_OOM, "host allocation failed");
+    b->o = o;
+    b->n = n;
+    b->st = static_cast<cudaStream_t>(o.stream);
+    b->tw = o.tile_cols;
+    b->chunk = o.graph_steps;
+    b->mode = o.mode == LBM_BATCH_PER_STEP ? LBM_BATCH_PER_STEP : LBM_BATCH_PERSISTENT;
+    b->inst.resize(n);
+    long long off = 0;
+    for (int i = 0; i < n; ++i) {
+        const lbm_cde_channel_desc& d = descs[i];
+        if (d.nx < 2 || d.nx > (1 << 24) || d.ny < 3 || d.ny > 65535) {
+            delete b;
+            return bfail(nullptr, LBM_E_ARG, "instance grid out of range (nx >= 2, 3 <= ny <= 65535)");
+        }
+        for (int side = 0; side < 2; ++side) {
+            const int k = side ? d.bc_hi_y : d.bc_lo_y;
+            if (k != LBM_BC_NOFLUX_NODE && k != LBM_BC_BOUNCEBACK && k != LBM_BC_PERIODIC) {
+                delete b;
+                return bfail(nullptr, LBM_E_ARG, "batch walls: PERIODIC, NOFLUX_NODE or BOUNCEBACK");
+            }
+        }
+        if ((d.bc_lo_y == LBM_BC_PERIODIC) != (d.bc_hi_y == LBM_BC_PERIODIC)) {
+            delete b;
+            return bfail(nullptr, LBM_E_ARG, "periodic y needs both faces periodic");
+        }
+        // A = (3 D + I/2)^-1 (Eq. 36 with the MRT-A factor 1/3); D must be SPD
+        const double* D = d.D;
+        if (!(D[0] > 0) || !(D[0] * D[3] - D[1] * D[2] > 0) || std::fabs(D[1] - D[2]) > 1e-12 * std::fabs(D[0])) {
+            delete b;
+            return bfail(nullptr, LBM_E_NOT_SPD, "instance D not symmetric positive definite");
+        }
+        const double Ai[4] = {3 * D[0] + 0.5, 3 * D[1], 3 * D[2], 3 * D[3] + 0.5};
+        const double det = Ai[0] * Ai[3] - Ai[1] * Ai[2];
+        const double A[4] = {Ai[3] / det, -Ai[1] / det, -Ai[2] / det, Ai[0] / det};
+        lbm::InstDev& I = b->inst[i];
+        I.nx = (int)d.nx;
+        I.ny = (int)d.ny;
+        I.off = off;
+        I.bc_lo = d.bc_lo_y;
+        I.bc_hi = d.bc_hi_y;
+        I.xref0 = (long long)llround(d.x_ref0);
+        I.vref = d.x_ref_velocity;
+        I.urow = d.u_row_dev;
+        batch_coef(d, A, I.c);
+        off += d.nx * d.ny;
+    }
+    b->ncat = off;
+    b->inst_dev = static_cast<lbm::InstDev*>(balloc(b, sizeof(lbm::InstDev) * n));
+    for (int p = 0; p < 2; ++p) b->buf[p] = static_cast<float*>(balloc(b, sizeof(float) * 9 * (size_t)off));
+    b->sync = static_cast<unsigned*>(balloc(b, 64));
+    b->status = reinterpret_cast<int*>(b->sync + 4);
+    b->kdev = reinterpret_cast<long long*>(b->sync + 6);
+    b->moments = static_cast<double*>(balloc(b, sizeof(double) * 3 * (size_t)n * b->chunk));
+    if (!b->inst_dev || !b->buf[0] || !b->buf[1] || !b->sync || !b->moments) {
+        lbm_cde_batch_destroy(b);
+        return bfail(nullptr, LBM_E_OOM, "batch allocation failed");
+    }
+    cudaMemsetAsync(b->sync, 0, 64, b->st);
+    lbm_status s = rebuild_tiles(b);
+    if (s != LBM_OK) {
+        lbm_cde_batch_destroy(b);
+        return bfail(nullptr, s, "tile setup failed");
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_batch_destroy(lbm_cde_batch_t b)
+{
+    if (!b) return LBM_OK;
+    cudaStreamSynchronize(b->st);
+    drop_graph(b);
+    bfree(b, b->inst_dev);
+    bfree(b, b->tiles_dev);
+    bfree(b, b->partials);
+    bfree(b, b->buf[0]);
+    bfree(b, b->buf[1]);
+    bfree(b, b->sync);
+    bfree(b, b->moments);
+    delete b;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_batch_cells(lbm_cde_batch_t b, int64_t* ncat)
+{
+    if (!b || !ncat) return bfail(b, LBM_E_ARG, "NULL argument");
+    *ncat = b->ncat;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_batch_set_phi(lbm_cde_batch_t b, const float* phi_dev)
+{
+    if (!b || !phi_dev) return bfail(b, LBM_E_ARG, "NULL argument");
+    lbm::k_batch_init<<<152 * 8, 256, 0, b->st>>>(b->inst_dev, b->n, phi_dev, b->buf[0], b->ncat);
+    BCK(b, cudaGetLastError());
+    BCK(b, cudaMemsetAsync(b->sync, 0, 64, b->st));
+    b->t = 0;
+    b->ready = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_batch_get_phi(lbm_cde_batch_t b, float* phi_dev)
+{
+    if (!b || !phi_dev) return bfail(b, LBM_E_ARG, "NULL argument");
+    if (!b->ready) return bfail(b, LBM_E_STATE, "set_phi first");
+    lbm::k_batch_phi<<<152 * 8, 256, 0, b->st>>>(b->buf[b->t & 1], b->ncat, phi_dev);
+    BCK(b, cudaGetLastError());
+    return LBM_OK;
+}
+
+// Runs nsteps steps; the moments of every step go to moments_host
+// ([nsteps][n][3], may be NULL). Each full chunk replays the captured graph.
+lbm_status lbm_cde_batch_run(lbm_cde_batch_t b, int64_t nsteps, double* moments_host)
+{
+    if (!b || nsteps < 0) return bfail(b, LBM_E_ARG, "bad argument");
+    if (!b->ready) return bfail(b, LBM_E_STATE, "set_phi first");
+    int64_t done = 0;
+    while (done < nsteps) {
+        const int len = (int)std::min<int64_t>(b->chunk, nsteps - done);
+        const long long first = b->t + 1;      // moments ring slot of step k is (k-1) mod chunk
+        if (len == b->chunk && b->use_graph) {
+            lbm_status s = ensure_graph(b);
+            if (s != LBM_OK) return s;
+        }
+        if (len == b->chunk && b->use_graph && b->graph) {
+            BCK(b, cudaGraphLaunch(b->graph, b->st));
+        } else {
+            lbm::BatchArgs a = batch_args(b, len);
+            BCK(b, launch_batch(b, a));
+        }
+        if (moments_host) {
+            for (int s = 0; s < len; ++s) {
+                const long long slot = (first + s - 1) % b->chunk;
+                BCK(b, cudaMemcpyAsync(moments_host + (done + s) * 3 * b->n, b->moments + slot * 3 * b->n,
+                                       sizeof(double) * 3 * b->n, cudaMemcpyDeviceToHost, b->st));
+            }
+        }
+        b->t += len;
+        done += len;
+    }
+    BCK(b, cudaStreamSynchronize(b->st));
+    int st = 0;
+    BCK(b, cudaMemcpy(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) return bfail(b, (lbm_status)st, "a grid barrier timed out (state is no longer valid)");
+    return LBM_OK;
+}
+
+// Times candidate execution modes and tile widths on `steps` steps each, then
+// keeps the fastest (the state is restored afterwards). Writes the choice to
+// *mode_out / *tile_out (may be NULL).
+lbm_status lbm_cde_batch_autotune(lbm_cde_batch_t b, int64_t steps, int32_t* mode_out, int32_t* tile_out)
+{
+    if (!b || steps < 1) return bfail(b, LBM_E_ARG, "bad argument");
+    if (!b->ready) return bfail(b, LBM_E_STATE, "set_phi first");
+    const size_t sb = sizeof(float) * 9 * (size_t)b->ncat;
+    // save the state and step index
+    float* save = static_cast<float*>(balloc(b, sb));
+    if (!save) return bfail(b, LBM_E_OOM, "autotune buffer allocation failed");
+    BCK(b, cudaMemcpyAsync(save, b->buf[b->t & 1], sb, cudaMemcpyDeviceToDevice, b->st));
+    const long long t_save = b->t;
+    const int modes[2] = {LBM_BATCH_PERSISTENT, LBM_BATCH_PER_STEP};
+    const int tws[3] = {128, 256, 512};
+    float best = 1e30f;
+    int best_mode = b->mode, best_tw = b->tw;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int m : modes)
+        for (int tw : tws) {
+            b->mode = m;
+            if (b->tw != tw) {
+                b->tw = tw;
+                lbm_status s = rebuild_tiles(b);
+                if (s != LBM_OK) return s;
+            }
+            lbm_status s = lbm_cde_batch_run(b, std::min<int64_t>(steps, b->chunk), nullptr);  // warm
+            if (s != LBM_OK) return s;
+            cudaEventRecord(e0, b->st);
+            s = lbm_cde_batch_run(b, steps, nullptr);
+            cudaEventRecord(e1, b->st);
+            cudaEventSynchronize(e1);
+            if (s != LBM_OK) return s;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_mode = m;
+                best_tw = tw;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->mode = best_mode;
+    if (b->tw != best_tw) {
+        b->tw = best_tw;
+        lbm_status s = rebuild_tiles(b);
+        if (s != LBM_OK) return s;
+    }
+    // restore: state into buf[t_save & 1], step index on the device
+    BCK(b, cudaMemcpyAsync(b->buf[t_save & 1], save, sb, cudaMemcpyDeviceToDevice, b->st));
+    BCK(b, cudaMemcpyAsync(b->kdev, &t_save, sizeof(long long), cudaMemcpyHostToDevice, b->st));
+    BCK(b, cudaStreamSynchronize(b->st));
+    bfree(b, save);
+    b->t = t_save;
+    if (mode_out) *mode_out = best_mode;
+    if (tile_out) *tile_out = best_tw;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_batch_config(lbm_cde_batch_t b, int32_t mode, int32_t tile_cols)
+{
+    if (!b || (mode != LBM_BATCH_PERSISTENT && mode != LBM_BATCH_PER_STEP) ||
+        (tile_cols != 128 && tile_cols != 256 && tile_cols != 512))
+        return bfail(b, LBM_E_ARG, "bad mode or tile width");
+    b->mode = mode;
+    if (b->tw != tile_cols) {
+        b->tw = tile_cols;
+        return rebuild_tiles(b);
+    }
+    return LBM_OK;
+}
+
+const char* lbm_cde_batch_last_error(lbm_cde_batch_t b) { return b ? b->err.c_str() : g_batch_err.c_str(); }
+
+}  // extern "C"

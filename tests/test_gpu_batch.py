@@ -1,0 +1,165 @@
+"""Batched channels (lbm_cde_batch_*): parity of every instance and of the
+per-step Eq. 47 moments with the FP64 oracle, determinism across execution
+modes and tile widths, equality with a standalone run, the bounded grid
+barrier, and the Taylor-Aris dispersion coefficient against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from _common import rel_l2
+from paper_1404_2363_gb300 import _native as N
+from paper_1404_2363_gb300.batch import Batch, alpha_L, mean_velocity, poiseuille_row, sigma2
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [  # nx, ny, walls, U, D
+    (96, 9, "noflux", 0.05, [[0.02, 0.0], [0.0, 0.02]]),
+    (200, 17, "noflux", 0.10, [[0.05, 0.01], [0.01, 0.03]]),
+    (333, 33, "bounceback", 0.08, [[0.03, 0.0], [0.0, 0.03]]),
+    (130, 12, "noflux", 0.0, [[0.1, 0.02], [0.02, 0.06]]),
+    (257, 20, "periodic", 0.06, [[0.04, -0.01], [-0.01, 0.05]]),
+]
+
+
+def channels(specs=SPECS):
+    out, phis = [], []
+    for (nx, ny, wall, U, D) in specs:
+        u = poiseuille_row(ny, U)
+        cols = np.arange(nx)
+        pulse = ((cols / nx >= 0.3) & (cols / nx <= 0.36)).astype(np.float32)
+        phi = np.broadcast_to(pulse, (ny, nx)).astype(np.float32) + 0.05
+        out.append({"nx": nx, "ny": ny, "bc": (wall, wall), "D": D, "u_row": u,
+                    "x_ref0": float(np.round(0.33 * nx)), "x_ref_velocity": mean_velocity(u)})
+        phis.append(phi)
+    return out, phis
+
+
+def oracle_run(O, ch, phi0, nsteps):
+    """phi after every step and the Eq. 47 sums of the same definition."""
+    nx, ny = ch["nx"], ch["ny"]
+    kind = {"noflux": O.NOFLUX_NODE, "bounceback": O.BOUNCEBACK, "periodic": O.PERIODIC}[ch["bc"][0]]
+    p = O.Params(nx=nx, ny=ny, bc_lo=kind, bc_hi=kind, A=O.A_from_D(np.array(ch["D"])))
+    u = np.zeros((2, ny, nx))
+    u[0] = ch["u_row"][0].astype(np.float64)[:, None]
+    u = u.reshape(2, -1)
+    f = O.init_eq(p, phi0.astype(np.float64).reshape(-1), u)
+    w = np.ones(ny)
+    if kind != O.PERIODIC:
+        w[0] = w[-1] = 0.5
+    mom = []
+    post = np.empty_like(f)
+    for k in range(1, nsteps + 1):
+        f = O.step(p, f, u, post)
+        phi = O.phi_of(p, f).reshape(ny, nx)
+        pb = (w[:, None] * phi).sum(axis=0)
+        c = int(np.round(ch["x_ref0"] + ch["x_ref_velocity"] * k))
+        xi = (np.arange(nx) - c) % nx
+        xi = np.where(xi >= (nx + 1) // 2, xi - nx, xi).astype(np.float64)
+        mom.append([pb.sum(), (pb * xi).sum(), (pb * xi * xi).sum()])
+    return phi, np.array(mom)
+
+
+def test_instances_and_moments_match_oracle(O):
+    chs, phis = channels()
+    nsteps = 150
+    b = Batch(chs, mode="persistent", graph_steps=32)
+    b.set_phi(phis)
+    mom = b.run(nsteps)
+    got = [g.cpu().numpy().astype(np.float64) for g in b.get_phi()]
+    b.close()
+    for i, ch in enumerate(chs):
+        want_phi, want_mom = oracle_run(O, ch, phis[i], nsteps)
+        assert rel_l2(got[i], want_phi) <= 1e-5, i
+        assert np.abs(mom[:, i, 0] / want_mom[:, 0] - 1).max() < 2e-6
+        assert np.abs(sigma2(mom[:, i]) / sigma2(want_mom) - 1).max() < 1e-5
+
+
+def test_modes_and_tiles_are_bitwise_identical():
+    chs, phis = channels()
+    ref = None
+    for mode, tile, gsteps in [("persistent", 256, 16), ("per_step", 128, 16), ("persistent", 512, 7),
+                               ("per_step", 256, 1)]:
+        b = Batch(chs, mode=mode, tile_cols=tile, graph_steps=gsteps)
+        b.set_phi(phis)
+        mom = b.run(53)
+        phi = torch.cat([g.reshape(-1) for g in b.get_phi()]).cpu().numpy()
+        b.close()
+        if ref is None:
+            ref = (mom, phi)
+        else:
+            assert np.array_equal(mom, ref[0]), (mode, tile)
+            assert np.array_equal(phi, ref[1]), (mode, tile)
+    b = Batch(chs)
+    b.set_phi(phis)
+    b.autotune(steps=16)
+    b.set_phi(phis)
+    mom = b.run(53)
+    assert np.array_equal(mom, ref[0])
+
+
+def test_instance_equals_standalone_solver():
+    from paper_1404_2363_gb300.solver import Solver
+
+    chs, phis = channels()
+    b = Batch(chs)
+    b.set_phi(phis)
+    b.run(40, moments=False)
+    got = [g.cpu().numpy() for g in b.get_phi()]
+    for i, ch in enumerate(chs):
+        s = Solver(nx=ch["nx"], ny=ch["ny"], bc=ch["bc"])
+        s.set_D(np.array(ch["D"]))
+        s.set_velocity(torch.from_numpy(ch["u_row"]).cuda(), kind="row")
+        s.set_phi(torch.from_numpy(phis[i]).cuda())
+        s.step(40)
+        want = s.get_phi().cpu().numpy()
+        assert np.abs(got[i] - want).max() <= 1e-6 * np.abs(want).max(), i
+
+
+def test_barrier_timeout_is_reported_without_hanging():
+    """A zero-cycle barrier limit makes every waiting CTA give up at once: the run
+    returns LBM_E_TIMEOUT and the context stays usable."""
+    chs, phis = channels()
+    b = Batch(chs, mode="persistent", barrier_timeout_cycles=0)
+    b.set_phi(phis)
+    with pytest.raises(N.LbmError) as e:
+        b.run(8)
+    assert e.value.status == N.LBM_E_TIMEOUT
+    b.close()
+    b = Batch(chs, mode="per_step")
+    b.set_phi(phis)
+    m = b.run(4)
+    assert np.isfinite(m).all()
+
+
+def test_taylor_aris_alpha_matches_oracle_recursion(O):
+    """Sec. 3.2 channel (W = 32, 33 nodes, Neumann walls), tau = 2, Pe = 4:
+    the dispersion coefficient from the batch moments (slope of sigma^2 over the
+    last 1000 of 4000 steps) equals the oracle's converged exact-moment value."""
+    tau, Pe, W, nx = 2.0, 4.0, 32, 2048
+    alpha = (tau - 0.5) / 3
+    U = 3 * alpha * Pe / (2 * W)
+    ny = W + 1
+    u = poiseuille_row(ny, U)
+    cols = np.arange(nx)
+    phi0 = np.broadcast_to(((cols / nx >= 0.197) & (cols / nx <= 0.203)).astype(np.float32), (ny, nx)).copy()
+    s = [1.0, 1.1, 1.1, None, 1 / tau, None, 1 / tau, 1.2, 1.2]
+    ch = {"nx": nx, "ny": ny, "D": np.eye(2) * alpha, "u_row": u, "s": s, "tie": False,
+          "x_ref0": 0.2 * nx, "x_ref_velocity": mean_velocity(u)}
+    b = Batch([ch, dict(ch)])
+    b.set_phi([phi0, phi0])
+    mom = b.run(4000)
+    b.close()
+    a_gpu = (sigma2(mom[-1, 0]) - sigma2(mom[-1001, 0])) / 2000.0
+    assert np.array_equal(mom[:, 0], mom[:, 1])
+    # oracle: converged exact x-moment recursion (tests/test_oracle_taylor_aris.py pins it)
+    p = O.Params(q=9, nx=1, ny=ny, bc_lo=O.NOFLUX_NODE, bc_hi=O.NOFLUX_NODE, A=np.eye(2) / tau,
+                 s=np.array([1.0, 1.1, 1.1, 0, 1 / tau, 0, 1 / tau, 1.2, 1.2]), tie=False)
+    _, _, Mi, _ = O.tables(p)
+    F0 = np.zeros((3, 9, ny))
+    for yy in range(ny):
+        F0[0, :, yy] = Mi @ O.meq(p, 1.0, [float(u[0, yy]), 0.0])
+    wy = np.ones(ny)
+    wy[0] = wy[-1] = 0.5
+    a_or = O.alpha_series(O.channel_moments(p, u[0].astype(np.float64), F0, wy, 30000))[-1]
+    assert abs(a_gpu / a_or - 1) < 2e-4, (a_gpu, a_or)
+    assert abs(alpha_L(mom[:, 0], 500)[-1] / a_or - 1) < 1e-3
