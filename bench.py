@@ -446,11 +446,13 @@ def main():
     variants = {}
     for vs in ("f16", "bf16"):
         sv, *_ = make_solver(vs)
+        shape = sv.autotune(20)
         dtv = time_steps(sv, args.steps, args.warmup)
         sv.close()
         av = ncell * B_LU[vs] / (dtv / args.steps) / 1e9
         variants[vs] = {"MLUPS": ncell * args.steps / dtv / 1e6, "bytes_per_lu": B_LU[vs],
-                        "achieved_gbs": av, "frac_of_" + peak_kind + "_hbm": av / peak}
+                        "achieved_gbs": av, "frac_of_" + peak_kind + "_hbm": av / peak,
+                        "launch": {"block": shape[0], "vec": shape[1]}}
     torch.cuda.empty_cache()
 
     variants["taylor_aris_batch"] = batch_bench(args.steps)

@@ -155,9 +155,18 @@ lbm_status lbm_cde_set_phi(lbm_cde_t h, const float* phi_dev);
 lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps);
 
 /* Sets the launch shape of the step kernel: block threads per CTA along x
- * (a multiple of 32 in [32, 1024]) and vec cells per thread (1 or 2). Results
- * do not depend on the shape. Errors: LBM_E_ARG. */
+ * (a multiple of 32 in [32, 256]) and vec cells per thread (1 or 2; 3 selects
+ * the row-walking kernel of the D2Q9 16-bit storage forms). Results do not
+ * depend on the shape. Errors: LBM_E_ARG. */
 lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec);
+
+/* Autotuner: times every launch shape (block 64/128/256 x vec 1/2, and the
+ * row-walking kernel for D2Q9 16-bit storage) over `steps` steps from the
+ * current state, keeps the fastest, and restores the state and step count.
+ * With LBMCDE_TUNE_CACHE set, the choice is read from / appended to that text
+ * file (lines "key block vec"; the key holds lattice, storage, grid, velocity
+ * kind, walls and GPU name). Needs set_phi first; synchronising. */
+lbm_status lbm_cde_autotune(lbm_cde_t h, int64_t steps, int32_t* block_out, int32_t* vec_out);
 
 /* Number of steps taken since the last set_phi / set_state. */
 lbm_status lbm_cde_get_time(lbm_cde_t h, int64_t* t_out);

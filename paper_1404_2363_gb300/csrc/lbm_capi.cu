@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -417,10 +418,121 @@ lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps)
 lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec)
 {
     if (!h) return fail(h, LBM_E_ARG, "NULL handle");
-    if (block < 32 || block > 1024 || block % 32 != 0 || (vec != 1 && vec != 2))
-        return fail(h, LBM_E_ARG, "block must be a multiple of 32 in [32, 1024], vec 1 or 2");
+    if (block < 32 || block > 256 || block % 32 != 0 || vec < 1 || vec > 3 ||
+        (vec == 3 && !(h->q == 9 && h->neq)))
+        return fail(h, LBM_E_ARG, "block must be a multiple of 32 in [32, 256]; vec 1 or 2 "
+                                  "(3: row-walking kernel, D2Q9 16-bit storage only)");
     h->cfg.block = block;
     h->cfg.vec = vec;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: times the candidate launch shapes on the current state and keeps
+// the fastest. Choices are cached in a text file (one "key block vec" line per
+// configuration) named by LBMCDE_TUNE_CACHE, keyed by lattice, storage, grid,
+// velocity kind, walls and GPU name.
+// ---------------------------------------------------------------------------
+static std::string tune_key(lbm_cde_t h)
+{
+    cudaDeviceProp prop{};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    std::string gpu(prop.name);
+    for (char& ch : gpu)
+        if (ch == ' ') ch = '_';
+    char buf[256];
+    snprintf(buf, sizeof(buf), "q%d_s%d_%lldx%lldx%lld_u%d_bc%d%d_%s", h->q, h->d.storage, (long long)h->d.nx,
+             (long long)h->d.ny, (long long)h->d.nz, h->ukind, h->d.bc_lo_y, h->d.bc_hi_y, gpu.c_str());
+    return buf;
+}
+
+static bool tune_cache_lookup(const std::string& key, int* block, int* vec)
+{
+    const char* path = getenv("LBMCDE_TUNE_CACHE");
+    if (!path) return false;
+    FILE* fp = fopen(path, "r");
+    if (!fp) return false;
+    char k[256];
+    int b = 0, v = 0;
+    bool found = false;
+    while (fscanf(fp, "%255s %d %d", k, &b, &v) == 3)
+        if (key == k) {
+            *block = b;
+            *vec = v;
+            found = true;
+        }
+    fclose(fp);
+    return found;
+}
+
+static void tune_cache_store(const std::string& key, int block, int vec)
+{
+    const char* path = getenv("LBMCDE_TUNE_CACHE");
+    if (!path) return;
+    FILE* fp = fopen(path, "a");
+    if (!fp) return;
+    fprintf(fp, "%s %d %d\n", key.c_str(), block, vec);
+    fclose(fp);
+}
+
+lbm_status lbm_cde_autotune(lbm_cde_t h, int64_t steps, int32_t* block_out, int32_t* vec_out)
+{
+    if (!h || steps < 1) return fail(h, LBM_E_ARG, "bad argument");
+    if (!h->ready) return fail(h, LBM_E_STATE, "set_phi must come before autotune");
+    const std::string key = tune_key(h);
+    int cb = 0, cv = 0;
+    if (tune_cache_lookup(key, &cb, &cv) && lbm_cde_set_launch(h, cb, cv) == LBM_OK) {
+        if (block_out) *block_out = cb;
+        if (vec_out) *vec_out = cv;
+        return LBM_OK;
+    }
+    size_t sb = 0;
+    lbm_cde_state_bytes(h, &sb);
+    void* save = dev_alloc(h, sb);
+    if (!save) return fail(h, LBM_E_OOM, "autotune buffer allocation failed");
+    int64_t t0 = 0;
+    lbm_status s = lbm_cde_get_state(h, save, &t0);
+    if (s != LBM_OK) {
+        dev_free(h, save);
+        return s;
+    }
+    const LaunchCfg keep = h->cfg;
+    float best = 1e30f;
+    LaunchCfg best_cfg = keep;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks[3] = {64, 128, 256};
+    const int maxvec = (h->q == 9 && h->neq) ? 3 : 2;
+    for (int vec = 1; vec <= maxvec && s == LBM_OK; ++vec)
+        for (int bi = 0; bi < 3 && s == LBM_OK; ++bi) {
+            if (vec == 3 && bi > 0) break;          // the row-walking kernel has one shape
+            h->cfg = LaunchCfg{blocks[bi], vec};
+            s = lbm_cde_set_state(h, save, t0);
+            if (s == LBM_OK) s = lbm_cde_step(h, 2);     // warm
+            cudaEventRecord(e0, h->st);
+            if (s == LBM_OK) s = lbm_cde_step(h, steps);
+            cudaEventRecord(e1, h->st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (s == LBM_OK && ms < best) {
+                best = ms;
+                best_cfg = h->cfg;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->cfg = s == LBM_OK ? best_cfg : keep;
+    lbm_status r = lbm_cde_set_state(h, save, t0);
+    dev_free(h, save);
+    if (s != LBM_OK) return s;
+    if (r != LBM_OK) return r;
+    tune_cache_store(key, h->cfg.block, h->cfg.vec);
+    if (block_out) *block_out = h->cfg.block;
+    if (vec_out) *vec_out = h->cfg.vec;
     return LBM_OK;
 }
 

@@ -8,11 +8,27 @@ namespace lbm {
 template <class L, int STORE, int UK, bool WALLS>
 static cudaError_t step_vec(LaunchCfg cfg, const StepArgs& a, cudaStream_t st)
 {
-    const int per = cfg.block * cfg.vec;
+    if constexpr (L::Q == 9 && STORE != ST_F32) {
+        if (cfg.vec == 3) {
+            // row-walking variant of the offset storage (fixed 256-thread shape)
+            dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)((a.ny + NEQ_ROWS - 1) / NEQ_ROWS), 1);
+            k_step_neq_d2q9<STORE, UK, WALLS><<<grid, 256, 0, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
+    const int vec = cfg.vec == 2 ? 2 : 1;
+    const int per = cfg.block * vec;
     dim3 grid((unsigned)((a.nx + per - 1) / per), (unsigned)a.ny, (unsigned)a.nz);
     dim3 block((unsigned)cfg.block);
-    if (cfg.vec == 2) k_step<L, STORE, UK, WALLS, 2><<<grid, block, 0, st>>>(a);
-    else k_step<L, STORE, UK, WALLS, 1><<<grid, block, 0, st>>>(a);
+    // 32-bit offsets when every plane and velocity offset fits
+    const bool idx32 = (long long)(L::Q + 3) * a.ncell < (1LL << 31);
+    if (idx32) {
+        if (vec == 2) k_step<L, STORE, UK, WALLS, 2, int><<<grid, block, 0, st>>>(a);
+        else k_step<L, STORE, UK, WALLS, 1, int><<<grid, block, 0, st>>>(a);
+    } else {
+        if (vec == 2) k_step<L, STORE, UK, WALLS, 2, long long><<<grid, block, 0, st>>>(a);
+        else k_step<L, STORE, UK, WALLS, 1, long long><<<grid, block, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -138,6 +138,11 @@ class Solver:
     def set_launch(self, block=256, vec=1):
         self._ck(self.L.lbm_cde_set_launch(self.h, int(block), int(vec)), "lbm_cde_set_launch")
 
+    def autotune(self, steps=20):
+        b, v = ctypes.c_int32(), ctypes.c_int32()
+        self._ck(self.L.lbm_cde_autotune(self.h, int(steps), ctypes.byref(b), ctypes.byref(v)), "lbm_cde_autotune")
+        return b.value, v.value
+
     def step(self, n=1):
         self._ck(self.L.lbm_cde_step(self.h, int(n)), "lbm_cde_step")
 
