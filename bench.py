@@ -333,6 +333,33 @@ def e2e_run(store: str, steps: int):
             "note": f"one lbm_cde_run_host call of {steps} steps; per-step bytes are the call's copies / steps"}
 
 
+def d3q15_bench(steps: int):
+    """The D3Q15 workload: 384^3 periodic, divergence-free random velocity field,
+    full anisotropic D, FP32 (132 B per lattice update)."""
+    import torch
+
+    from paper_1404_2363_gb300 import workloads as W
+    from paper_1404_2363_gb300.solver import Solver
+
+    n = 384
+    wl = W.d3q15_workload(n)
+    s = Solver(lattice=15, nx=n, ny=n, nz=n)
+    s.set_D(wl["D"])
+    s.set_velocity(torch.from_numpy(wl["u"].astype(np.float32)).cuda())
+    s.set_phi(torch.from_numpy(wl["phi0"].astype(np.float32)).cuda())
+    del wl
+    shape = s.autotune(10)
+    k = max(50, min(steps, 600))
+    dt = time_steps(s, k, 5)
+    s.close()
+    peak, kind = peaks()
+    cells = n ** 3
+    gbs = cells * 132 / (dt / k) / 1e9
+    return {"grid": [n, n, n], "steps": k, "MLUPS": cells * k / dt / 1e6, "bytes_per_lu": 132,
+            "achieved_gbs": gbs, f"frac_of_{kind}_hbm": gbs / peak,
+            "launch": {"block": shape[0], "vec": shape[1]}}
+
+
 def batch_bench(steps: int):
     """The Taylor-Aris batch workload: 64 uneven channels in one launch per graph
     chunk, moments every step; mode and tile width from the autotuner."""
@@ -455,6 +482,8 @@ def main():
                         "launch": {"block": shape[0], "vec": shape[1]}}
     torch.cuda.empty_cache()
 
+    variants["d3q15_384"] = d3q15_bench(args.steps)
+    torch.cuda.empty_cache()
     variants["taylor_aris_batch"] = batch_bench(args.steps)
     torch.cuda.empty_cache()
     adjoint = adjoint_cost(store, ms_forward=dt / args.steps * 1e3)
