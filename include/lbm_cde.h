@@ -81,6 +81,12 @@ enum {
     LBM_STORE_BF16_NEQ = 2  /* g_i in BF16, phi in FP32                              */
 };
 
+/* Collision models (Sec. 3): MRT-A is the modified model (Eq. 30-31 with the
+ * equilibrium of Eq. 15 / 37); the MRT-B models use the unmodified S of Eq. 24
+ * with the equilibria of Eq. 38 (B1), Eq. 39 (B2) or Eq. 37 (B3). The MRT-B
+ * models exist for D2Q9; B1 and B2 need FP32 storage. */
+enum { LBM_MRT_A = 0, LBM_MRT_B1 = 1, LBM_MRT_B2 = 2, LBM_MRT_B3 = 3 };
+
 /* Velocity representations (lbm_cde_set_velocity). */
 enum {
     LBM_U_NONE = 0,         /* u = 0                                                 */
@@ -110,6 +116,8 @@ typedef struct {
     void (*free_)(void* ptr, void* ctx);
     void* alloc_ctx;
     void* stream;            /* cudaStream_t for every launch (NULL: legacy stream)  */
+    int32_t model;           /* LBM_MRT_A (default) / LBM_MRT_B1 / B2 / B3; for the B
+                                models alpha1, alpha2 are fixed by their equilibria  */
 } lbm_cde_desc;
 
 /* Fills *d with defaults for a periodic grid (F32 storage, default alpha and
@@ -126,8 +134,9 @@ lbm_status lbm_cde_destroy(lbm_cde_t h);
 
 /* Sets the diffusion tensor. D is dim x dim, row-major, host memory, lattice
  * units. The relaxation block is A = (D / k + I / 2)^-1 with
- * k = 2/3 + alpha1/8 + alpha2/12 (Eq. 36) or 2/3 + 55 alpha1/54 + alpha2/216
- * (Eq. A.6); A enters S through Eq. 30-31 / A.5.
+ * k = 2/3 + alpha1/8 + alpha2/12 (Eq. 36, MRT-A), 2/3 + alpha1/24 (Eq. 29, the
+ * MRT-B models) or 2/3 + 55 alpha1/54 + alpha2/216 (Eq. A.6); A enters S through
+ * Eq. 30-31 / 24 / A.5.
  * Errors: LBM_E_ARG (NULL), LBM_E_NOT_SPD (D not symmetric to 1e-12 relative or
  * not positive definite, or k <= 0). */
 lbm_status lbm_cde_set_D(lbm_cde_t h, const double* D);
@@ -271,6 +280,7 @@ typedef struct {
     const float* u_row_dev;  /* device [2][ny] velocity per row (borrowed), or NULL (u = 0) */
     double x_ref0;           /* moment reference centre at t = 0 (node index) */
     double x_ref_velocity;   /* its drift per step */
+    int32_t model;           /* LBM_MRT_A / B1 / B2 / B3 */
 } lbm_cde_channel_desc;
 
 typedef struct {

@@ -44,9 +44,11 @@ class LbmDesc(ctypes.Structure):
         ("free_", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
         ("stream", ctypes.c_void_p),
+        ("model", ctypes.c_int32),
     ]
 
 
+LBM_MRT_A, LBM_MRT_B1, LBM_MRT_B2, LBM_MRT_B3 = 0, 1, 2, 3
 LBM_BATCH_AUTO, LBM_BATCH_PERSISTENT, LBM_BATCH_PER_STEP = 0, 1, 2
 
 
@@ -62,6 +64,7 @@ class ChannelDesc(ctypes.Structure):
         ("u_row_dev", ctypes.c_void_p),
         ("x_ref0", ctypes.c_double),
         ("x_ref_velocity", ctypes.c_double),
+        ("model", ctypes.c_int32),
     ]
 
 

@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _native as N
-from .solver import BC, _TorchAllocator
+from .solver import BC, MODELS, _TorchAllocator
 
 MODES = {"auto": N.LBM_BATCH_AUTO, "persistent": N.LBM_BATCH_PERSISTENT, "per_step": N.LBM_BATCH_PER_STEP}
 
@@ -49,6 +49,7 @@ class Batch:
                 d.u_row_dev = u.data_ptr()
             d.x_ref0 = float(ch.get("x_ref0", 0.0))
             d.x_ref_velocity = float(ch.get("x_ref_velocity", 0.0))
+            d.model = MODELS[ch.get("model", "A")]
             self.shapes.append((d.ny, d.nx))
         o = N.BatchOpts()
         self.L.lbm_cde_batch_opts_init(ctypes.byref(o))

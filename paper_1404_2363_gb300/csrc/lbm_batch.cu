@@ -293,9 +293,10 @@ __global__ void k_batch_init(const InstDev* __restrict__ inst, int ninst, const 
         const InstDev& I = inst[lo];
         const int y = (int)((c - I.off) / I.nx);
         const float ux = I.urow ? I.urow[y] : 0.f, uy = I.urow ? I.urow[I.ny + y] : 0.f;
-        const float p = phi0[c];
+        float fe[9];
+        feq_full<D2Q9>(I.c, phi0[c], ux, uy, 0.f, fe);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[(long long)i * ncat + c] = p * feq_unit<D2Q9>(I.c, i, ux, uy, 0.f);
+        for (int i = 0; i < 9; ++i) f[(long long)i * ncat + c] = fe[i];
     }
 }
 
@@ -409,6 +410,7 @@ static void bfree(lbm_cde_batch_t b, void* p)
 
 static void batch_coef(const lbm_cde_channel_desc& d, const double A[4], lbm::Coef& c)
 {
+    const int model = d.model;
     const double defaults[9] = {1.0, 1.1, 1.1, 0, 1.0, 0, 1.0, 1.2, 1.2};
     double s[15] = {0};
     for (int k = 0; k < 9; ++k) s[k] = std::isnan(d.s[k]) ? defaults[k] : d.s[k];
@@ -421,11 +423,18 @@ static void batch_coef(const lbm_cde_channel_desc& d, const double A[4], lbm::Co
     for (int a = 0; a < 2; ++a)
         for (int bb = 0; bb < 2; ++bb) {
             c.A[a * 2 + bb] = (float)A[a * 2 + bb];
-            c.C[a * 2 + bb] = (float)((A[a * 2 + bb] / 2.0 - (a == bb ? 1.0 : 0.0)) * s[4 + 2 * bb]);
+            // Eq. 30-31 couplings for MRT-A; the MRT-B models use the unmodified S of Eq. 24
+            c.C[a * 2 + bb] = model == LBM_MRT_A
+                                  ? (float)((A[a * 2 + bb] / 2.0 - (a == bb ? 1.0 : 0.0)) * s[4 + 2 * bb])
+                                  : 0.f;
         }
-    // MRT-A equilibrium, alpha1 = -8, alpha2 = 8 (Eq. 37), f^eq of Eq. 17
+    // equilibrium: Eq. 37 (MRT-A, B3), Eq. 38 (B1), Eq. 39 (B2); f^eq weights of Eq. 17
     c.meq1 = -2.f;
-    c.meq2 = 2.f;
+    c.meq2 = model == LBM_MRT_B1 ? 1.f : 2.f;
+    c.b1 = (model == LBM_MRT_B1 || model == LBM_MRT_B2) ? 3.f : 0.f;
+    c.b2 = (model == LBM_MRT_B1 || model == LBM_MRT_B2) ? -3.f : 0.f;
+    c.g7 = (model == LBM_MRT_B1 || model == LBM_MRT_B2) ? 1.f : 0.f;
+    c.g8 = c.g7;
     c.w0 = (float)(20.0 / 36.0);
     c.wa = (float)(8.0 / 144.0);
     c.wd = (float)(8.0 / 144.0);
@@ -570,6 +579,10 @@ lbm_status lbm_cde_batch_create(const lbm_cde_channel_desc* descs, int32_t n, co
         if (d.nx < 2 || d.nx > (1 << 24) || d.ny < 3 || d.ny > 65535) {
             delete b;
             return bfail(nullptr, LBM_E_ARG, "instance grid out of range (nx >= 2, 3 <= ny <= 65535)");
+        }
+        if (d.model < LBM_MRT_A || d.model > LBM_MRT_B3) {
+            delete b;
+            return bfail(nullptr, LBM_E_ARG, "bad model");
         }
         for (int side = 0; side < 2; ++side) {
             const int k = side ? d.bc_hi_y : d.bc_lo_y;

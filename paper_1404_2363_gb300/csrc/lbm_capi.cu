@@ -97,10 +97,12 @@ static void dev_free(lbm_cde_t h, void* p)
 // ---------------------------------------------------------------------------
 // Parameters
 // ---------------------------------------------------------------------------
-static double diffusion_factor(int q, double a1, double a2)
+// The k in D = k (I - A/2) A^-1: Eq. 36 (modified S) or Eq. 29 (unmodified S
+// of the MRT-B models, k = 2/3 + alpha1/24) for D2Q9, Eq. A.6 for D3Q15.
+static double diffusion_factor(int q, double a1, double a2, int model = LBM_MRT_A)
 {
-    if (q == 9) return 2.0 / 3.0 + a1 / 8.0 + a2 / 12.0;          // Eq. 36
-    return 2.0 / 3.0 + 55.0 / 54.0 * a1 + a2 / 216.0;             // Eq. A.6
+    if (q == 9) return model == LBM_MRT_A ? 2.0 / 3.0 + a1 / 8.0 + a2 / 12.0 : 2.0 / 3.0 + a1 / 24.0;
+    return 2.0 / 3.0 + 55.0 / 54.0 * a1 + a2 / 216.0;
 }
 
 // Inverse of a small dense matrix (n <= 3) by cofactors; returns false if singular.
@@ -160,13 +162,20 @@ static void refresh_coef(lbm_cde_t h)
     }
     for (int k = 0; k < 15; ++k) c.s[k] = (float)s[k];
     for (int k = 0; k < 9; ++k) c.A[k] = 0.f, c.C[k] = 0.f;
+    const int model = h->d.model;
     for (int a = 0; a < n; ++a)
         for (int b = 0; b < n; ++b) {
             const double Aab = h->A[a * n + b];
             c.A[a * n + b] = (float)Aab;
-            // Eq. 30a-b / A.5: coupling of flux row a to q-moment b
-            c.C[a * n + b] = (float)((Aab / 2.0 - (a == b ? 1.0 : 0.0)) * s[4 + 2 * b]);
+            // Eq. 30a-b / A.5: coupling of flux row a to q-moment b (MRT-A only;
+            // the MRT-B models use the unmodified S of Eq. 24)
+            c.C[a * n + b] = model == LBM_MRT_A ? (float)((Aab / 2.0 - (a == b ? 1.0 : 0.0)) * s[4 + 2 * b]) : 0.f;
         }
+    const bool quad = model == LBM_MRT_B1 || model == LBM_MRT_B2;
+    c.b1 = quad ? 3.f : 0.f;
+    c.b2 = quad ? -3.f : 0.f;
+    c.g7 = quad ? 1.f : 0.f;
+    c.g8 = c.g7;
     const double a1 = h->alpha1, a2 = h->alpha2;
     if (h->q == 9) {
         c.meq1 = (float)(a1 / 4.0);
@@ -263,6 +272,14 @@ lbm_status lbm_cde_create(const lbm_cde_desc* desc, lbm_cde_t* out)
         return fail(nullptr, LBM_E_ARG, "walls need ny >= 3");
     if ((d.alloc == nullptr) != (d.free_ == nullptr))
         return fail(nullptr, LBM_E_ARG, "alloc and free_ must both be set or both NULL");
+    if (d.model < LBM_MRT_A || d.model > LBM_MRT_B3) return fail(nullptr, LBM_E_ARG, "bad model");
+    if (d.model != LBM_MRT_A && d.lattice != LBM_D2Q9)
+        return fail(nullptr, LBM_E_UNSUPPORTED, "the MRT-B models are D2Q9 only");
+    if ((d.model == LBM_MRT_B1 || d.model == LBM_MRT_B2) &&
+        (d.bc_lo_y == LBM_BC_DIRICHLET || d.bc_hi_y == LBM_BC_DIRICHLET))
+        return fail(nullptr, LBM_E_UNSUPPORTED, "Dirichlet walls need an equilibrium linear in u (MRT-A, MRT-B3)");
+    if ((d.model == LBM_MRT_B1 || d.model == LBM_MRT_B2) && d.storage != LBM_STORE_F32)
+        return fail(nullptr, LBM_E_UNSUPPORTED, "MRT-B1/B2 need FP32 storage (their equilibria are not linear in u)");
 
     lbm_cde_t h = new (std::nothrow) lbm_cde_s();
     if (!h) return fail(nullptr, LBM_E_OOM, "host allocation failed");
@@ -275,11 +292,17 @@ lbm_status lbm_cde_create(const lbm_cde_desc* desc, lbm_cde_t* out)
     h->st = static_cast<cudaStream_t>(d.stream);
     h->alpha1 = std::isnan(d.alpha1) ? (h->q == 9 ? -8.0 : -6.0 / 5.0) : d.alpha1;
     h->alpha2 = std::isnan(d.alpha2) ? (h->q == 9 ? 8.0 : 192.0) : d.alpha2;
+    if (d.model != LBM_MRT_A) {
+        // MRT-B1: m1 = (-2 + 3u^2), m2 = (1 - 3u^2) (Eq. 38); B2: m2 = (2 - 3u^2) (Eq. 39);
+        // B3: Eq. 37. Their u = 0 parts are alpha1 = -8 and alpha2 = 4 (B1) or 8.
+        h->alpha1 = -8.0;
+        h->alpha2 = d.model == LBM_MRT_B1 ? 4.0 : 8.0;
+    }
     const double defaults9[15] = {1.0, 1.1, 1.1, 0, 1.0, 0, 1.0, 1.2, 1.2, 0, 0, 0, 0, 0, 0};
     const double defaults15[15] = {1.0, 1.1, 1.1, 0, 1.0, 0, 1.0, 0, 1.0, 1.2, 1.2, 1.2, 1.2, 1.2, 1.2};
     for (int k = 0; k < 15; ++k)
         h->s[k] = std::isnan(d.s[k]) ? (h->q == 9 ? defaults9[k] : defaults15[k]) : d.s[k];
-    if (diffusion_factor(h->q, h->alpha1, h->alpha2) <= 0.0) {
+    if (diffusion_factor(h->q, h->alpha1, h->alpha2, h->d.model) <= 0.0) {
         delete h;
         return fail(nullptr, LBM_E_ARG, "alpha1/alpha2 give a non-positive diffusion factor (Eq. 36 / A.6)");
     }
@@ -351,7 +374,7 @@ lbm_status lbm_cde_set_D(lbm_cde_t h, const double* D)
             if (std::fabs(D[a * n + b] - D[b * n + a]) > 1e-12 * scale)
                 return fail(h, LBM_E_NOT_SPD, "D is not symmetric");
     if (!spd(n, D)) return fail(h, LBM_E_NOT_SPD, "D is not positive definite");
-    const double k = diffusion_factor(h->q, h->alpha1, h->alpha2);
+    const double k = diffusion_factor(h->q, h->alpha1, h->alpha2, h->d.model);
     double Ainv[9], A[9];
     for (int a = 0; a < n; ++a)
         for (int b = 0; b < n; ++b) Ainv[a * n + b] = D[a * n + b] / k + (a == b ? 0.5 : 0.0);
@@ -634,6 +657,8 @@ int32_t lbm_cde_adjoint_ngrad(int32_t lattice) { return lbm::adjoint_ngrad(latti
 
 static lbm_status adjoint_supported(lbm_cde_t h)
 {
+    if (h->d.model == LBM_MRT_B1 || h->d.model == LBM_MRT_B2)
+        return fail(h, LBM_E_UNSUPPORTED, "the adjoint covers the equilibria linear in u (MRT-A, MRT-B3)");
     if (h->d.storage != LBM_STORE_F32)
         return fail(h, LBM_E_UNSUPPORTED, "the adjoint needs FP32 state storage");
     if (h->d.bc_lo_y == LBM_BC_DIRICHLET || h->d.bc_hi_y == LBM_BC_DIRICHLET)
@@ -729,7 +754,7 @@ lbm_status lbm_cde_grad_rates(lbm_cde_t h, const double* g, double* dL_dD_host, 
         if (h->d.tie_q_rates)
             for (int b = 0; b < n; ++b) dA[b * n + b] += ds[4 + 2 * b];
         // A = (D/k + I/2)^-1  =>  dL/dD = -(1/k) A^T dL/dA A^T
-        const double kf = diffusion_factor(q, h->alpha1, h->alpha2);
+        const double kf = diffusion_factor(q, h->alpha1, h->alpha2, h->d.model);
         double T[9] = {0};
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < n; ++j) {

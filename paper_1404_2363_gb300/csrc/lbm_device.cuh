@@ -128,6 +128,41 @@ __device__ __forceinline__ float feq_unit(const Coef& c, int i, float ux, float 
     return fmaf(c.kd, eu, c.wd);
 }
 
+// Full equilibrium f^eq = M^T diag(1/|M_k|^2) m^eq(phi, u), including the u^2
+// terms of the MRT-B1/B2 equilibria (used for initial states).
+template <class L>
+__device__ __forceinline__ void feq_full(const Coef& c, float phi, float ux, float uy, float uz,
+                                         float (&fe)[L::Q])
+{
+    constexpr int Q = L::Q;
+    const float u[3] = {ux, uy, uz};
+    const float u2 = ux * ux + uy * uy + uz * uz;
+    float me[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) me[k] = 0.f;
+    me[0] = phi;
+    me[1] = fmaf(c.b1, u2, c.meq1) * phi;
+    me[2] = fmaf(c.b2, u2, c.meq2) * phi;
+#pragma unroll
+    for (int a = 0; a < L::DIM; ++a) {
+        me[3 + 2 * a] = u[a] * phi;
+        me[4 + 2 * a] = -u[a] * phi;
+    }
+    if (L::Q == 9) {
+        me[7] = c.g7 * (ux * ux - uy * uy) * phi;
+        me[8] = c.g8 * (ux * uy) * phi;
+    }
+#pragma unroll
+    for (int k = 0; k < Q; ++k) me[k] *= 1.0f / (float)row_norm2<L>(k);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) acc = fmaf((float)L::M(k, i), me[k], acc);
+        fe[i] = acc;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Collision in moment space for one node (Eq. 11, 13 with Eq. 31 / A.5, 14).
 // ---------------------------------------------------------------------------
@@ -153,9 +188,10 @@ __device__ __forceinline__ void collide(float (&f)[L::Q], float ux, float uy, fl
     const float u[3] = {ux, uy, uz};
     // non-equilibrium parts d = m - m^eq (Eq. 15 / A.3 with c1 = 1, c2 from Eq. 16 / A.4)
     float d[Q];
+    const float u2 = ux * ux + uy * uy + uz * uz;
     d[0] = 0.f;
-    d[1] = m[1] - c.meq1 * phi;
-    d[2] = m[2] - c.meq2 * phi;
+    d[1] = m[1] - fmaf(c.b1, u2, c.meq1) * phi;
+    d[2] = m[2] - fmaf(c.b2, u2, c.meq2) * phi;
 #pragma unroll
     for (int a = 0; a < L::DIM; ++a) {
         d[3 + 2 * a] = m[3 + 2 * a] - phi * u[a];
@@ -163,6 +199,10 @@ __device__ __forceinline__ void collide(float (&f)[L::Q], float ux, float uy, fl
     }
 #pragma unroll
     for (int k = 3 + 2 * L::DIM; k < Q; ++k) d[k] = m[k];
+    if (L::Q == 9) {   // MRT-B1/B2 second-order terms (zero coefficients otherwise)
+        d[7] -= c.g7 * (ux * ux - uy * uy) * phi;
+        d[8] -= c.g8 * (ux * uy) * phi;
+    }
     // relaxation m' = m - S d
     float mp[Q];
     mp[0] = m[0];
@@ -600,11 +640,10 @@ __global__ void k_init(const StepArgs a, const float* __restrict__ phi0)
         float ux, uy, uz;
         vel_at<UK, L::DIM>(a, c, y, s0, ux, uy, uz);
         const float p = phi0[c];
+        float fe[L::Q];
+        feq_full<L>(a.c, p, ux, uy, uz, fe);
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-            const float v = (STORE == ST_F32) ? p * feq_unit<L>(a.c, i, ux, uy, uz) : 0.f;
-            st_f(dst + (long long)i * a.ncell + c, v);
-        }
+        for (int i = 0; i < L::Q; ++i) st_f(dst + (long long)i * a.ncell + c, (STORE == ST_F32) ? fe[i] : 0.f);
         if (STORE != ST_F32) a.phi_dst[c] = p;
     }
 }

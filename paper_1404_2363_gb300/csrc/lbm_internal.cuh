@@ -27,6 +27,9 @@ struct Coef {
     float C[9];
     // f^eq_i = phi * (w_i + k_i e_i.u), Eq. 17 / its D3Q15 counterpart
     float w0, wa, wd, ka, kd;
+    // u^2 terms of the MRT-B1/B2 equilibria (Eq. 38-39), zero for MRT-A/B3:
+    //   m1 += b1 |u|^2 phi, m2 += b2 |u|^2 phi, m7 = g7 (ux^2 - uy^2) phi, m8 = g8 ux uy phi
+    float b1, b2, g7, g8;
 };
 
 struct StepArgs {

@@ -14,6 +14,7 @@ import torch
 from . import _native as N
 
 STORAGE = {"f32": N.LBM_STORE_F32, "f16": N.LBM_STORE_F16_NEQ, "bf16": N.LBM_STORE_BF16_NEQ}
+MODELS = {"A": N.LBM_MRT_A, "B1": N.LBM_MRT_B1, "B2": N.LBM_MRT_B2, "B3": N.LBM_MRT_B3}
 BC = {"periodic": N.LBM_BC_PERIODIC, "noflux": N.LBM_BC_NOFLUX_NODE,
       "bounceback": N.LBM_BC_BOUNCEBACK, "dirichlet": N.LBM_BC_DIRICHLET}
 
@@ -49,7 +50,7 @@ class Solver:
 
     def __init__(self, lattice=9, nx=64, ny=64, nz=1, storage="f32", bc=("periodic", "periodic"),
                  phi_w=(0.0, 0.0), alpha=None, s=None, tie=True, device=None, stream=None,
-                 torch_alloc=True):
+                 torch_alloc=True, model="A"):
         self.L = N.lib()
         if device is None:
             device = torch.device("cuda", torch.cuda.current_device())
@@ -73,6 +74,7 @@ class Solver:
                 if v is not None and not (isinstance(v, float) and math.isnan(v)):
                     d.s[k] = float(v)
         d.tie_q_rates = 1 if tie else 0
+        d.model = MODELS[model]
         self._alloc = None
         if torch_alloc:
             self._alloc = _TorchAllocator(self.device, self.stream)

@@ -27,6 +27,7 @@ class Case:
     D: np.ndarray = field(default_factory=lambda: W.D_ANISO.copy())
     umax: float = 0.05
     seed: int = 0
+    model: str = "A"
 
     @property
     def dim(self):
@@ -82,7 +83,8 @@ def oracle_params(O, case: Case):
               bc_lo=BC_ORACLE[case.bc[0]], bc_hi=BC_ORACLE[case.bc[1]],
               phi_w_lo=case.phi_w[0], phi_w_hi=case.phi_w[1])
     if case.lattice == 9:
-        return O.Params(A=O.A_from_D(case.D), **kw)
+        model = {"A": O.MRT_A, "B1": O.MRT_B1, "B2": O.MRT_B2, "B3": O.MRT_B3}[case.model]
+        return O.Params(A=O.A_from_D(case.D), model=model, **kw)
     return O.default_params_3d(A=O.A_from_D(case.D, q=15, alpha1=-1.2, alpha2=192.0), **kw)
 
 
@@ -102,7 +104,7 @@ def run_gpu(case: Case, phi0, a, sched, steps=None, solver_kw=None):
 
     steps = case.steps if steps is None else steps
     s = Solver(lattice=case.lattice, nx=case.nx, ny=case.ny, nz=case.nz, storage=case.storage,
-               bc=case.bc, phi_w=case.phi_w, **(solver_kw or {}))
+               bc=case.bc, phi_w=case.phi_w, model=case.model, **(solver_kw or {}))
     s.set_D(case.D)
     if a is not None:
         s.set_velocity(torch.from_numpy(a).cuda(), None if sched is None else torch.from_numpy(sched).cuda(),

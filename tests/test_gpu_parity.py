@@ -31,6 +31,10 @@ CASES_2D = [
     Case(storage="bf16", bc=("bounceback", "bounceback"), ukind="field"),
     Case(storage="f16", bc=("dirichlet", "dirichlet"), phi_w=(1.0, 0.25), ukind="field"),
     Case(storage="f32", nx=1, ny=5, ukind="none", sched=False, steps=50),
+    Case(storage="f32", model="B1", umax=0.1),
+    Case(storage="f32", model="B2", umax=0.1, bc=("noflux", "noflux"), ukind="row"),
+    Case(storage="f32", model="B3", umax=0.1, bc=("bounceback", "bounceback")),
+    Case(storage="bf16", model="B3"),
     Case(storage="f32", nx=33, ny=1, ukind="field", steps=50),
 ]
 
@@ -48,7 +52,7 @@ CASES_3D = [
 
 
 def _id(c):
-    return f"q{c.lattice}-{c.storage}-{c.bc[0]}-{c.bc[1]}-{c.ukind}-{c.nx}x{c.ny}x{c.nz}"
+    return f"q{c.lattice}-{c.model}-{c.storage}-{c.bc[0]}-{c.bc[1]}-{c.ukind}-{c.nx}x{c.ny}x{c.nz}"
 
 
 @pytest.mark.parametrize("case", CASES_2D + CASES_3D, ids=_id)
