@@ -392,7 +392,7 @@ def batch_bench(steps: int):
     gbs = cells * 72 / (dt / n) / 1e9
     return {"instances": len(chans), "cells": cells, "steps": n, "MLUPS": cells * n / dt / 1e6,
             "bytes_per_lu": 72, "achieved_gbs": gbs, f"frac_of_{kind}_hbm": gbs / peak,
-            "mode": mode, "tile_cols": tile,
+            "mode": mode, "tile_rows": tile,
             "timing": "host wall clock around lbm_cde_batch_run (graph replays + per-step moment copies)"}
 
 

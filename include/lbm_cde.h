@@ -285,7 +285,8 @@ typedef struct {
 
 typedef struct {
     int32_t mode;            /* LBM_BATCH_AUTO (persistent until autotuned) / PERSISTENT / PER_STEP */
-    int32_t tile_cols;       /* columns per tile: 128, 256 or 512 */
+    int32_t tile_rows;       /* rows per work tile (a tile is 32 columns x tile_rows rows, one
+                                warp), 1 .. 1024; default 16 */
     int32_t graph_steps;     /* steps per captured CUDA graph (ring of moments), 1 .. 4096 */
     int64_t barrier_timeout_cycles; /* clock64 cycles a CTA waits at a grid barrier before the
                                 launch gives up with LBM_E_TIMEOUT (default 2e9, about 1 s) */
@@ -318,12 +319,12 @@ lbm_status lbm_cde_batch_get_phi(lbm_cde_batch_t b, float* phi_dev);
  * then invalid until the next set_phi). */
 lbm_status lbm_cde_batch_run(lbm_cde_batch_t b, int64_t nsteps, double* moments_host);
 
-/* Times every execution mode x tile width on `steps` steps, keeps the fastest
- * (restoring the state and step count) and reports it. */
+/* Times every execution mode x tile height (8, 16, 32 rows) on `steps` steps,
+ * keeps the fastest (restoring the state and step count) and reports it. */
 lbm_status lbm_cde_batch_autotune(lbm_cde_batch_t b, int64_t steps, int32_t* mode_out, int32_t* tile_out);
 
-/* Selects an execution mode and tile width explicitly. */
-lbm_status lbm_cde_batch_config(lbm_cde_batch_t b, int32_t mode, int32_t tile_cols);
+/* Selects an execution mode and tile height explicitly. */
+lbm_status lbm_cde_batch_config(lbm_cde_batch_t b, int32_t mode, int32_t tile_rows);
 
 const char* lbm_cde_batch_last_error(lbm_cde_batch_t b);
 

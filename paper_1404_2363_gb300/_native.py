@@ -71,7 +71,7 @@ class ChannelDesc(ctypes.Structure):
 class BatchOpts(ctypes.Structure):
     _fields_ = [
         ("mode", ctypes.c_int32),
-        ("tile_cols", ctypes.c_int32),
+        ("tile_rows", ctypes.c_int32),
         ("graph_steps", ctypes.c_int32),
         ("barrier_timeout_cycles", ctypes.c_int64),
         ("alloc", ALLOC_FN),

@@ -20,7 +20,7 @@ MODES = {"auto": N.LBM_BATCH_AUTO, "persistent": N.LBM_BATCH_PERSISTENT, "per_st
 
 
 class Batch:
-    def __init__(self, channels, mode="auto", tile_cols=256, graph_steps=64, barrier_timeout_cycles=2_000_000_000,
+    def __init__(self, channels, mode="auto", tile_rows=16, graph_steps=64, barrier_timeout_cycles=2_000_000_000,
                  device=None, stream=None, torch_alloc=True):
         self.L = N.lib()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -54,7 +54,7 @@ class Batch:
         o = N.BatchOpts()
         self.L.lbm_cde_batch_opts_init(ctypes.byref(o))
         o.mode = MODES[mode]
-        o.tile_cols = tile_cols
+        o.tile_rows = tile_rows
         o.graph_steps = graph_steps
         o.barrier_timeout_cycles = int(barrier_timeout_cycles)
         self._alloc = None
@@ -116,8 +116,8 @@ class Batch:
                  "lbm_cde_batch_autotune")
         return {1: "persistent", 2: "per_step"}[mode.value], tile.value
 
-    def config(self, mode, tile_cols):
-        self._ck(self.L.lbm_cde_batch_config(self.h, MODES[mode], int(tile_cols)), "lbm_cde_batch_config")
+    def config(self, mode, tile_rows):
+        self._ck(self.L.lbm_cde_batch_config(self.h, MODES[mode], int(tile_rows)), "lbm_cde_batch_config")
 
 
 def sigma2(moments):

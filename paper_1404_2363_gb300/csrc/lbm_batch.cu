@@ -2,19 +2,21 @@
 // rates and row velocity profile) advanced together, with the moments of the
 // cross-section mean (Sec. 3.2, Eq. 46-47) reduced every step.
 //
-// Work unit ("tile"): one instance and a run of TW consecutive columns; a CTA
-// of TW threads walks all ny rows of its columns (walls at the two ends of
-// the walk), so the cross-section sum phi-bar(x) = sum_y w_y phi(x, y)
-// (trapezoid weights, walls on the nodes) stays in a register. Per tile the
-// partial moments sum phi-bar {1, xi, xi^2} go to a fixed slot (xi = x minus
-// an integer reference centre, wrapped to [-nx/2, nx/2)), and a fixed-order
-// pass sums them per instance, so the moments are deterministic.
+// Work unit ("tile"): one instance, 32 consecutive columns and a strip of at
+// most tile_rows rows; one warp walks the rows of its strip, keeping the strip's part of the cross-section sum phi-bar(x) = sum_y w_y
+// phi(x, y) (trapezoid weights, walls on the nodes) in a register. The moments
+// sum_x phi-bar(x) {1, xi, xi^2} are linear in phi-bar, so every tile adds its
+// strip's partial moments to a fixed slot (xi = x minus an integer reference
+// centre, wrapped to [-nx/2, nx/2)), and a fixed-order pass sums the slots per
+// instance: the moments are deterministic, and the strips keep the tiles small
+// and even so that no CTA waits long at the per-step barrier.
 //
 // Two execution modes, chosen by the autotuner:
-//   PERSISTENT : one cooperative launch runs K steps; CTAs take tiles from an
+//   PERSISTENT : one cooperative launch runs K steps; warps take tiles from an
 //                atomic counter, and a grid barrier (bounded spin, then
 //                LBM_E_TIMEOUT) separates the steps;
-//   PER_STEP   : one launch per step plus one moment-reduction launch.
+//   PER_STEP   : one launch per step (one 32 x 8 block per tile, one node per
+//                thread) plus one moment-reduction launch.
 // Either is captured once into a CUDA graph of K steps and replayed.
 #include <algorithm>
 #include <cmath>
@@ -43,7 +45,8 @@ struct InstDev {
 
 struct TileDev {
     int inst;
-    int x0;
+    int x0;       // first column
+    int y0, y1;   // row strip [y0, y1)
 };
 
 struct BatchArgs {
@@ -71,33 +74,42 @@ __device__ __forceinline__ long long wrap_ll(long long v, long long n)
     return v < 0 ? v + n : v;
 }
 
-// One tile of one step: pull-stream, walls, collide, store; returns the tile's
-// partial moments in red (thread 0).
-template <int TW>
-__device__ void batch_tile(const BatchArgs& a, long long t, long long k, const float* __restrict__ src,
-                           float* __restrict__ dst, Coef& cs, double* red3)
+// One warp tile of one step (32 columns x the rows [y0, y1) of one instance):
+// pull-stream, walls, collide, store, and the strip's partial moments, summed
+// over the warp; lane 0 ends with the sums. No block-level synchronisation:
+// the instance constants are read through L1.
+__device__ __forceinline__ void warp_tile(const BatchArgs& a, long long t, long long k,
+                                          const float* __restrict__ src, float* __restrict__ dst, int lane,
+                                          double* m)
 {
     const TileDev td = a.tiles[t];
     const InstDev& I = a.inst[td.inst];
-    __syncthreads();
-    if (threadIdx.x == 0) cs = I.c;
-    __syncthreads();
+    const Coef& cs = I.c;
     const int nx = I.nx, ny = I.ny;
     const long long N = a.ncat;
-    const int x = td.x0 + threadIdx.x;
+    const int x = td.x0 + lane;
     const bool live = x < nx;
     const int xc = live ? x : nx - 1;
     const int xs[3] = {xc + 1 == nx ? 0 : xc + 1, xc, xc == 0 ? nx - 1 : xc - 1};
     const long long base = I.off;
-    float col = 0.f, comp = 0.f;   // Kahan sum of w_y phi over the column
-    for (int y = 0; y < ny; ++y) {
+    const bool walls = I.bc_lo != BC_PERIODIC;
+    float col = 0.f, comp = 0.f;   // Kahan sum of w_y phi over the strip of this column
+    // software pipeline: the pulls of row y+1 are requested before row y is computed
+    auto pull_row = [&](int y, float* f) {
         const int ys[3] = {y + 1 == ny ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};
-        float f[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i)
             f[i] = __ldg(src + (long long)i * N + base + (long long)ys[D2Q9::ey(i) + 1] * nx + xs[D2Q9::ex(i) + 1]);
-        const bool lo = y == 0 && I.bc_lo != BC_PERIODIC;
-        const bool hi = y == ny - 1 && I.bc_hi != BC_PERIODIC;
+    };
+    float fnext[9];
+    pull_row(td.y0, fnext);
+    for (int y = td.y0; y < td.y1; ++y) {
+        float f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = fnext[i];
+        if (y + 1 < td.y1) pull_row(y + 1, fnext);
+        const bool lo = walls && y == 0;
+        const bool hi = walls && y == ny - 1;
         if (lo || hi) {
             const int kind = lo ? I.bc_lo : I.bc_hi;
             const long long cell = base + (long long)y * nx + xc;
@@ -122,58 +134,56 @@ __device__ void batch_tile(const BatchArgs& a, long long t, long long k, const f
 #pragma unroll
             for (int i = 0; i < 9; ++i) dst[(long long)i * N + cell] = f[i];
         }
-        const float w = (I.bc_lo != BC_PERIODIC && (y == 0 || y == ny - 1)) ? 0.5f : 1.0f;
+        const float w = (walls && (y == 0 || y == ny - 1)) ? 0.5f : 1.0f;
         const float yv = w * phi - comp;
         const float tv = col + yv;
         comp = (tv - col) - yv;
         col = tv;
     }
-    // moments of phi-bar about the integer reference centre
+    // moments of the strip's phi-bar about the integer reference centre
     const long long cref = I.xref0 + (long long)llround(I.vref * (double)k);
     long long xi = wrap_ll((long long)x - cref, nx);
     if (xi >= (nx + 1) / 2) xi -= nx;
     const double pb = live ? (double)col : 0.0;
-    double m0 = pb, m1 = pb * (double)xi, m2 = pb * (double)xi * (double)xi;
-    // block sum: warp shuffles then shared memory, fixed order
+    m[0] = pb;
+    m[1] = pb * (double)xi;
+    m[2] = pb * (double)xi * (double)xi;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        m0 += __shfl_down_sync(0xffffffffu, m0, off);
-        m1 += __shfl_down_sync(0xffffffffu, m1, off);
-        m2 += __shfl_down_sync(0xffffffffu, m2, off);
-    }
-    __shared__ double wred[TW / 32][3];
-    const int warp = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        wred[warp][0] = m0;
-        wred[warp][1] = m1;
-        wred[warp][2] = m2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s0 = 0, s1 = 0, s2 = 0;
-        for (int w = 0; w < TW / 32; ++w) {
-            s0 += wred[w][0];
-            s1 += wred[w][1];
-            s2 += wred[w][2];
-        }
-        red3[0] = s0;
-        red3[1] = s1;
-        red3[2] = s2;
+        m[0] += __shfl_down_sync(0xffffffffu, m[0], off);
+        m[1] += __shfl_down_sync(0xffffffffu, m[1], off);
+        m[2] += __shfl_down_sync(0xffffffffu, m[2], off);
     }
 }
 
-__device__ void reduce_instance(const BatchArgs& a, int i, const double* part, double* out)
+// Moments of step k for every instance: one warp per instance sums the tile
+// partials with a fixed lane assignment and a fixed shuffle tree.
+__device__ void reduce_moments(const BatchArgs& a, long long k, const double* part)
 {
-    const InstDev& I = a.inst[i];
-    double s0 = 0, s1 = 0, s2 = 0;
-    for (long long t = I.tile0; t < I.tile0 + I.ntiles; ++t) {
-        s0 += part[t * 3 + 0];
-        s1 += part[t * 3 + 1];
-        s2 += part[t * 3 + 2];
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = gw; i < a.ninst; i += nw) {
+        const InstDev& I = a.inst[i];
+        double s0 = 0, s1 = 0, s2 = 0;
+        for (long long t = I.tile0 + lane; t < I.tile0 + I.ntiles; t += 32) {
+            s0 += part[t * 3 + 0];
+            s1 += part[t * 3 + 1];
+            s2 += part[t * 3 + 2];
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            s0 += __shfl_down_sync(0xffffffffu, s0, off);
+            s1 += __shfl_down_sync(0xffffffffu, s1, off);
+            s2 += __shfl_down_sync(0xffffffffu, s2, off);
+        }
+        if (lane == 0) {
+            double* out = a.moments + (((k - 1) % a.ring) * a.ninst + i) * 3;
+            out[0] = s0;
+            out[1] = s1;
+            out[2] = s2;
+        }
     }
-    out[0] = s0;
-    out[1] = s1;
-    out[2] = s2;
 }
 
 // Grid barrier with a bounded wait: returns false (and latches LBM_E_TIMEOUT)
@@ -209,18 +219,12 @@ __device__ bool grid_barrier(const BatchArgs& a)
     return ok != 0;
 }
 
-__device__ __forceinline__ double* moment_slot(const BatchArgs& a, long long k, int i)
-{
-    return a.moments + (((k - 1) % a.ring) * a.ninst + i) * 3;
-}
-
 // B_0 sits in buf[0], so B_{k-1} is in buf[(k-1) & 1] and B_k goes to buf[k & 1].
-template <int TW>
-__global__ void __launch_bounds__(TW) k_batch_persistent(const BatchArgs a)
+// Every warp takes tiles from the step's counter (lane 0 fetches the next index
+// while the current tile runs); a grid barrier closes each step.
+__global__ void __launch_bounds__(256, 4) k_batch_persistent(const BatchArgs a)
 {
-    __shared__ Coef cs;
-    __shared__ double red3[3];
-    __shared__ long long tile_s;
+    const int lane = threadIdx.x & 31;
     const long long t0 = *a.kdev;
     for (int s = 0; s < a.nsteps; ++s) {
         const long long k = t0 + 1 + s;
@@ -228,50 +232,113 @@ __global__ void __launch_bounds__(TW) k_batch_persistent(const BatchArgs a)
         float* dst = a.buf[k & 1];
         double* part = a.partials + (long long)(k & 1) * a.ntiles * 3;
         if (blockIdx.x == 0 && threadIdx.x == 0) a.counter[(k + 1) & 1] = 0u;
-        while (true) {
-            __syncthreads();
-            if (threadIdx.x == 0) tile_s = (long long)atomicAdd(a.counter + (k & 1), 1u);
-            __syncthreads();
-            const long long t = tile_s;
-            if (t >= a.ntiles) break;
-            batch_tile<TW>(a, t, k, src, dst, cs, red3);
-            if (threadIdx.x == 0) {
-                part[t * 3 + 0] = red3[0];
-                part[t * 3 + 1] = red3[1];
-                part[t * 3 + 2] = red3[2];
+        unsigned* ctr = a.counter + (k & 1);
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(ctr, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        while ((long long)t < a.ntiles) {
+            unsigned tn = 0;
+            if (lane == 0) tn = atomicAdd(ctr, 1u);
+            double m[3];
+            warp_tile(a, t, k, src, dst, lane, m);
+            if (lane == 0) {
+                part[(long long)t * 3 + 0] = m[0];
+                part[(long long)t * 3 + 1] = m[1];
+                part[(long long)t * 3 + 2] = m[2];
             }
+            t = __shfl_sync(0xffffffffu, tn, 0);
         }
         if (!grid_barrier(a)) return;
-        // moments of step k, one thread per instance
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.ninst; i += gridDim.x * blockDim.x)
-            reduce_instance(a, i, part, moment_slot(a, k, i));
+        reduce_moments(a, k, part);
     }
 }
 
-template <int TW>
-__global__ void __launch_bounds__(TW) k_batch_step(const BatchArgs a)
+// Cell-parallel step for PER_STEP mode: one block of 32 x 8 threads per tile,
+// every thread one node (rows y0 + warp, +8, ...), so each thread has all nine
+// pulls in flight at once; the column sums of the strip meet in shared memory.
+__global__ void __launch_bounds__(256) k_batch_step_cells(const BatchArgs a)
 {
-    __shared__ Coef cs;
-    __shared__ double red3[3];
-    const long long k = *a.kdev + 1;
-    const float* src = a.buf[(k - 1) & 1];
-    float* dst = a.buf[k & 1];
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
     const long long t = blockIdx.x;
-    batch_tile<TW>(a, t, k, src, dst, cs, red3);
-    if (threadIdx.x == 0) {
+    const long long k = *a.kdev + 1;
+    const float* __restrict__ src = a.buf[(k - 1) & 1];
+    float* __restrict__ dst = a.buf[k & 1];
+    const TileDev td = a.tiles[t];
+    const InstDev& I = a.inst[td.inst];
+    const Coef& cs = I.c;
+    const int nx = I.nx, ny = I.ny;
+    const long long N = a.ncat;
+    const int x = td.x0 + lane;
+    const bool live = x < nx;
+    const int xc = live ? x : nx - 1;
+    const int xs[3] = {xc + 1 == nx ? 0 : xc + 1, xc, xc == 0 ? nx - 1 : xc - 1};
+    const long long base = I.off;
+    const bool walls = I.bc_lo != BC_PERIODIC;
+    float col = 0.f;
+    for (int y = td.y0 + wy; y < td.y1; y += 8) {
+        const int ys[3] = {y + 1 == ny ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};
+        float f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            f[i] = __ldg(src + (long long)i * N + base + (long long)ys[D2Q9::ey(i) + 1] * nx + xs[D2Q9::ex(i) + 1]);
+        const bool lo = walls && y == 0;
+        const bool hi = walls && y == ny - 1;
+        if (lo || hi) {
+            const int kind = lo ? I.bc_lo : I.bc_hi;
+            const long long cell = base + (long long)y * nx + xc;
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                if (D2Q9::ey(i) != 0 && ((D2Q9::ey(i) == 1) == lo)) {
+                    if (kind == BC_BOUNCE) f[i] = __ldg(src + (long long)opposite<D2Q9>(i) * N + cell);
+                    else f[i] = f[mirror_y<D2Q9>(i)];
+                }
+        }
+        float ux = 0.f, uy = 0.f;
+        if (I.urow) {
+            ux = __ldg(I.urow + y);
+            uy = __ldg(I.urow + ny + y);
+        }
+        float phi = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) phi += f[i];
+        collide<D2Q9>(f, ux, uy, 0.f, cs);
+        if (live) {
+            const long long cell = base + (long long)y * nx + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) dst[(long long)i * N + cell] = f[i];
+        }
+        col += (walls && (y == 0 || y == ny - 1)) ? 0.5f * phi : phi;
+    }
+    __shared__ float cols[8][32];
+    cols[wy][lane] = col;
+    __syncthreads();
+    if (wy != 0) return;
+    double pb = 0.0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) pb += (double)cols[r][lane];
+    if (!live) pb = 0.0;
+    const long long cref = I.xref0 + (long long)llround(I.vref * (double)k);
+    long long xi = wrap_ll((long long)x - cref, nx);
+    if (xi >= (nx + 1) / 2) xi -= nx;
+    double m0 = pb, m1 = pb * (double)xi, m2 = pb * (double)xi * (double)xi;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        m0 += __shfl_down_sync(0xffffffffu, m0, off);
+        m1 += __shfl_down_sync(0xffffffffu, m1, off);
+        m2 += __shfl_down_sync(0xffffffffu, m2, off);
+    }
+    if (lane == 0) {
         double* part = a.partials + (long long)(k & 1) * a.ntiles * 3;
-        part[t * 3 + 0] = red3[0];
-        part[t * 3 + 1] = red3[1];
-        part[t * 3 + 2] = red3[2];
+        part[t * 3 + 0] = m0;
+        part[t * 3 + 1] = m1;
+        part[t * 3 + 2] = m2;
     }
 }
 
-__global__ void k_batch_moments(const BatchArgs a)
+__global__ void __launch_bounds__(256) k_batch_moments(const BatchArgs a)
 {
     const long long k = *a.kdev + 1;
-    const double* part = a.partials + (long long)(k & 1) * a.ntiles * 3;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.ninst; i += gridDim.x * blockDim.x)
-        reduce_instance(a, i, part, moment_slot(a, k, i));
+    reduce_moments(a, k, a.partials + (long long)(k & 1) * a.ntiles * 3);
 }
 
 __global__ void k_batch_advance(long long* kdev, int n)
@@ -311,7 +378,6 @@ __global__ void k_batch_phi(const float* __restrict__ f, long long ncat, float* 
     }
 }
 
-template <int TW>
 static cudaError_t launch_mode(int mode, const BatchArgs& a, int grid_persistent, long long* kdev,
                                cudaStream_t st)
 {
@@ -320,27 +386,27 @@ static cudaError_t launch_mode(int mode, const BatchArgs& a, int grid_persistent
         cudaError_t e = cudaMemsetAsync(a.counter, 0, 2 * sizeof(unsigned), st);
         if (e != cudaSuccess) return e;
         void* args[] = {(void*)&a};
-        e = cudaLaunchCooperativeKernel((const void*)k_batch_persistent<TW>, dim3(grid_persistent),
-                                                    dim3(TW), args, 0, st);
+        e = cudaLaunchCooperativeKernel((const void*)k_batch_persistent, dim3(grid_persistent), dim3(256), args,
+                                        0, st);
         if (e != cudaSuccess) return e;
         k_batch_advance<<<1, 1, 0, st>>>(kdev, a.nsteps);
         return cudaGetLastError();
     }
+    const unsigned nbm = (unsigned)((a.ninst + 7) / 8);
     for (int s = 0; s < a.nsteps; ++s) {
-        k_batch_step<TW><<<(unsigned)a.ntiles, TW, 0, st>>>(a);
-        k_batch_moments<<<(a.ninst + 127) / 128, 128, 0, st>>>(a);
+        k_batch_step_cells<<<(unsigned)a.ntiles, 256, 0, st>>>(a);
+        k_batch_moments<<<nbm, 256, 0, st>>>(a);
         k_batch_advance<<<1, 1, 0, st>>>(kdev, 1);
     }
     return cudaGetLastError();
 }
 
-template <int TW>
 static int persistent_grid()
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_persistent<TW>, TW, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_persistent, 256, 0);
     return std::max(1, per) * sms;
 }
 
@@ -366,11 +432,12 @@ struct lbm_cde_batch_s {
     long long t = 0;
     bool ready = false;
     int mode = LBM_BATCH_PERSISTENT;
-    int tw = 256;
+    int rows = 16;                 // rows per warp tile
     int chunk = 64;                // steps per graph replay
-    cudaGraphExec_t graph = nullptr;   // one chunk of steps, built lazily for (mode, tw)
+    cudaGraphExec_t graph = nullptr;   // one chunk of steps, built lazily for (mode, rows)
     int graph_key[2] = {-1, -1};
     bool use_graph = true;
+    double* stage = nullptr;       // pinned host staging for one chunk of moments
     cudaStream_t st = nullptr;
     std::string err;
 };
@@ -467,11 +534,7 @@ static lbm::BatchArgs batch_args(lbm_cde_batch_t b, int nsteps)
 
 static cudaError_t launch_batch(lbm_cde_batch_t b, const lbm::BatchArgs& a)
 {
-    switch (b->tw) {
-        case 128: return lbm::launch_mode<128>(b->mode, a, lbm::persistent_grid<128>(), b->kdev, b->st);
-        case 512: return lbm::launch_mode<512>(b->mode, a, lbm::persistent_grid<512>(), b->kdev, b->st);
-        default: return lbm::launch_mode<256>(b->mode, a, lbm::persistent_grid<256>(), b->kdev, b->st);
-    }
+    return lbm::launch_mode(b->mode, a, lbm::persistent_grid(), b->kdev, b->st);
 }
 
 static void drop_graph(lbm_cde_batch_t b)
@@ -487,7 +550,7 @@ static void drop_graph(lbm_cde_batch_t b)
 // parity live on the device, so the same graph serves every chunk.
 static lbm_status ensure_graph(lbm_cde_batch_t b)
 {
-    if (b->graph && b->graph_key[0] == b->mode && b->graph_key[1] == b->tw) return LBM_OK;
+    if (b->graph && b->graph_key[0] == b->mode && b->graph_key[1] == b->rows) return LBM_OK;
     drop_graph(b);
     cudaStream_t cap = nullptr;
     BCK(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -512,16 +575,24 @@ static lbm_status ensure_graph(lbm_cde_batch_t b)
         return LBM_OK;
     }
     b->graph_key[0] = b->mode;
-    b->graph_key[1] = b->tw;
+    b->graph_key[1] = b->rows;
     return LBM_OK;
 }
 
+// Warp tiles: 32 columns x a strip of at most b->rows rows.
 static lbm_status rebuild_tiles(lbm_cde_batch_t b)
 {
     b->tiles.clear();
     for (int i = 0; i < b->n; ++i) {
         b->inst[i].tile0 = (long long)b->tiles.size();
-        for (int x0 = 0; x0 < b->inst[i].nx; x0 += b->tw) b->tiles.push_back({i, x0});
+        const int ny = b->inst[i].ny;
+        const int nstrip = (ny + b->rows - 1) / b->rows;
+        for (int sidx = 0; sidx < nstrip; ++sidx) {
+            // strips of nearly equal height
+            const int y0 = (int)((long long)ny * sidx / nstrip);
+            const int y1 = (int)((long long)ny * (sidx + 1) / nstrip);
+            for (int x0 = 0; x0 < b->inst[i].nx; x0 += 32) b->tiles.push_back({i, x0, y0, y1});
+        }
         b->inst[i].ntiles = (long long)b->tiles.size() - b->inst[i].tile0;
     }
     bfree(b, b->tiles_dev);
@@ -545,7 +616,7 @@ lbm_status lbm_cde_batch_opts_init(lbm_cde_batch_opts* o)
     if (!o) return bfail(nullptr, LBM_E_ARG, "NULL opts");
     std::memset(o, 0, sizeof(*o));
     o->mode = LBM_BATCH_AUTO;
-    o->tile_cols = 256;
+    o->tile_rows = 16;
     o->graph_steps = 64;
     o->barrier_timeout_cycles = 2000000000LL;
     return LBM_OK;
@@ -560,8 +631,7 @@ lbm_status lbm_cde_batch_create(const lbm_cde_channel_desc* descs, int32_t n, co
     if (opts) o = *opts;
     else lbm_cde_batch_opts_init(&o);
     if ((o.alloc == nullptr) != (o.free_ == nullptr)) return bfail(nullptr, LBM_E_ARG, "alloc/free_ mismatch");
-    if (o.tile_cols != 128 && o.tile_cols != 256 && o.tile_cols != 512)
-        return bfail(nullptr, LBM_E_ARG, "tile_cols must be 128, 256 or 512");
+    if (o.tile_rows < 1 || o.tile_rows > 1024) return bfail(nullptr, LBM_E_ARG, "tile_rows in [1, 1024]");
     if (o.graph_steps < 1 || o.graph_steps > 4096) return bfail(nullptr, LBM_E_ARG, "graph_steps in [1, 4096]");
     if (o.barrier_timeout_cycles < 0) return bfail(nullptr, LBM_E_ARG, "negative barrier timeout");
     lbm_cde_batch_t b = new (std::nothrow) lbm_cde_batch_s();
@@ -569,7 +639,7 @@ lbm_status lbm_cde_batch_create(const lbm_cde_channel_desc* descs, int32_t n, co
     b->o = o;
     b->n = n;
     b->st = static_cast<cudaStream_t>(o.stream);
-    b->tw = o.tile_cols;
+    b->rows = o.tile_rows;
     b->chunk = o.graph_steps;
     b->mode = o.mode == LBM_BATCH_PER_STEP ? LBM_BATCH_PER_STEP : LBM_BATCH_PERSISTENT;
     b->inst.resize(n);
@@ -642,6 +712,7 @@ lbm_status lbm_cde_batch_destroy(lbm_cde_batch_t b)
     if (!b) return LBM_OK;
     cudaStreamSynchronize(b->st);
     drop_graph(b);
+    if (b->stage) cudaFreeHost(b->stage);
     bfree(b, b->inst_dev);
     bfree(b, b->tiles_dev);
     bfree(b, b->partials);
@@ -701,11 +772,19 @@ lbm_status lbm_cde_batch_run(lbm_cde_batch_t b, int64_t nsteps, double* moments_
             BCK(b, launch_batch(b, a));
         }
         if (moments_host) {
-            for (int s = 0; s < len; ++s) {
-                const long long slot = (first + s - 1) % b->chunk;
-                BCK(b, cudaMemcpyAsync(moments_host + (done + s) * 3 * b->n, b->moments + slot * 3 * b->n,
-                                       sizeof(double) * 3 * b->n, cudaMemcpyDeviceToHost, b->st));
-            }
+            // the ring slots of this chunk form at most two contiguous runs; copy
+            // them into pinned staging, then into the caller's array
+            if (!b->stage) BCK(b, cudaMallocHost(&b->stage, sizeof(double) * 3 * b->n * b->chunk));
+            const size_t row = (size_t)3 * b->n;
+            const long long s0 = (first - 1) % b->chunk;
+            const long long run1 = std::min<long long>(len, b->chunk - s0);
+            BCK(b, cudaMemcpyAsync(b->stage, b->moments + s0 * row, sizeof(double) * row * run1,
+                                   cudaMemcpyDeviceToHost, b->st));
+            if (run1 < len)
+                BCK(b, cudaMemcpyAsync(b->stage + run1 * row, b->moments, sizeof(double) * row * (len - run1),
+                                       cudaMemcpyDeviceToHost, b->st));
+            BCK(b, cudaStreamSynchronize(b->st));
+            std::memcpy(moments_host + done * row, b->stage, sizeof(double) * row * len);
         }
         b->t += len;
         done += len;
@@ -731,17 +810,17 @@ lbm_status lbm_cde_batch_autotune(lbm_cde_batch_t b, int64_t steps, int32_t* mod
     BCK(b, cudaMemcpyAsync(save, b->buf[b->t & 1], sb, cudaMemcpyDeviceToDevice, b->st));
     const long long t_save = b->t;
     const int modes[2] = {LBM_BATCH_PERSISTENT, LBM_BATCH_PER_STEP};
-    const int tws[3] = {128, 256, 512};
+    const int tws[3] = {8, 16, 32};
     float best = 1e30f;
-    int best_mode = b->mode, best_tw = b->tw;
+    int best_mode = b->mode, best_tw = b->rows;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     for (int m : modes)
         for (int tw : tws) {
             b->mode = m;
-            if (b->tw != tw) {
-                b->tw = tw;
+            if (b->rows != tw) {
+                b->rows = tw;
                 lbm_status s = rebuild_tiles(b);
                 if (s != LBM_OK) return s;
             }
@@ -763,8 +842,8 @@ lbm_status lbm_cde_batch_autotune(lbm_cde_batch_t b, int64_t steps, int32_t* mod
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->mode = best_mode;
-    if (b->tw != best_tw) {
-        b->tw = best_tw;
+    if (b->rows != best_tw) {
+        b->rows = best_tw;
         lbm_status s = rebuild_tiles(b);
         if (s != LBM_OK) return s;
     }
@@ -779,14 +858,13 @@ lbm_status lbm_cde_batch_autotune(lbm_cde_batch_t b, int64_t steps, int32_t* mod
     return LBM_OK;
 }
 
-lbm_status lbm_cde_batch_config(lbm_cde_batch_t b, int32_t mode, int32_t tile_cols)
+lbm_status lbm_cde_batch_config(lbm_cde_batch_t b, int32_t mode, int32_t tile_rows)
 {
-    if (!b || (mode != LBM_BATCH_PERSISTENT && mode != LBM_BATCH_PER_STEP) ||
-        (tile_cols != 128 && tile_cols != 256 && tile_cols != 512))
-        return bfail(b, LBM_E_ARG, "bad mode or tile width");
+    if (!b || (mode != LBM_BATCH_PERSISTENT && mode != LBM_BATCH_PER_STEP) || tile_rows < 1 || tile_rows > 1024)
+        return bfail(b, LBM_E_ARG, "bad mode or tile height");
     b->mode = mode;
-    if (b->tw != tile_cols) {
-        b->tw = tile_cols;
+    if (b->rows != tile_rows) {
+        b->rows = tile_rows;
         return rebuild_tiles(b);
     }
     return LBM_OK;

@@ -26,7 +26,12 @@ def main():
     ap.add_argument("--ukind", default="field", choices=["none", "field"])
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--vec", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=0, help="run N Taylor-Aris channels (per-step mode) instead")
+    ap.add_argument("--tile", type=int, default=16, help="rows per batch warp tile")
+    ap.add_argument("--mode", default="per_step", choices=["per_step", "persistent"])
     args = ap.parse_args()
+    if args.batch:
+        return run_batch(args)
     n = args.n
     if args.lattice == 9:
         shape, dim = (n, n), 2
@@ -48,6 +53,24 @@ def main():
     m = s.sum_phi()
     s.close()
     print(f"ok lattice={args.lattice} storage={args.storage} n={n} steps={args.steps} sum_phi={m:.6e}")
+
+
+def run_batch(args):
+    from .batch import Batch, mean_velocity, poiseuille_row
+
+    chans = W.taylor_aris_batch(args.batch)
+    descs, phis = [], []
+    for c in chans:
+        u = poiseuille_row(c.ny, c.U)
+        descs.append({"nx": c.nx, "ny": c.ny, "D": np.eye(2) * c.alpha, "u_row": u, "tie": False,
+                      "s": [1.0, 1.1, 1.1, None, 1 / c.tau, None, 1 / c.tau, 1.2, 1.2],
+                      "x_ref0": 0.2 * c.nx, "x_ref_velocity": mean_velocity(u)})
+        phis.append(c.phi0().astype(np.float32))
+    b = Batch(descs, mode=args.mode, tile_rows=args.tile, graph_steps=1)
+    b.set_phi(phis)
+    m = b.run(args.steps)
+    b.close()
+    print(f"ok batch={args.batch} cells={b.ncat} steps={args.steps} m0={m[-1, 0, 0]:.6e}")
 
 
 if __name__ == "__main__":

@@ -183,3 +183,36 @@ def test_inverse_problem_recovers_D():
         opt.step(closure)
     est = D_of(theta).detach().numpy()
     assert np.allclose(est, D_true, rtol=2e-3, atol=2e-5), est
+
+
+def test_d3q15_adjoint_matches_oracle_and_fd(O):
+    """The same reverse-time kernel on the D3Q15 lattice (Appendix A): dL/dphi0 and
+    dL/da against the FP64 oracle adjoint, dL/dD against FP64 central differences."""
+    D = np.array([[0.03, 0.004, -0.003], [0.004, 0.025, 0.002], [-0.003, 0.002, 0.035]])
+    case = Case(lattice=15, nx=12, ny=10, nz=9, steps=20, D=D)
+    phi0, a, sched = case.inputs()
+    g = np.random.default_rng(4).standard_normal(case.shape)
+    s = Solver(lattice=15, nx=case.nx, ny=case.ny, nz=case.nz)
+    s.set_D(D)
+    s.set_velocity(torch.from_numpy(a).cuda(), torch.from_numpy(sched).cuda())
+    s.forward_ckpt(torch.from_numpy(phi0).cuda(), case.steps)
+    dphi0, dD, _, da = s.backward(torch.from_numpy(g.astype(np.float32)).cuda(), want_da=True)
+    s.close()
+    wp, _, wa = oracle_grads(O, case, phi0, a, sched, g)
+    assert rel_l2(dphi0.cpu().numpy().astype(np.float64), wp) < 1e-5
+    assert rel_l2(da.cpu().numpy().astype(np.float64), wa) < 1e-4
+    uf = case.u_of_t(a, sched)
+    h = 1e-6
+    for (i, j) in ((0, 0), (0, 1), (1, 2), (2, 2)):
+        vals = []
+        for sgn in (1, -1):
+            Dp = D.copy()
+            Dp[i, j] += sgn * h
+            if i != j:
+                Dp[j, i] += sgn * h
+            p = oracle_params(O, Case(lattice=15, nx=case.nx, ny=case.ny, nz=case.nz, D=Dp))
+            phi = O.run(p, phi0.astype(np.float64).reshape(-1), case.steps, u_of_t=uf)
+            vals.append(float((g.reshape(-1) * phi).sum()))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        an = dD[i, j] + (dD[j, i] if i != j else 0.0)
+        assert abs(an - fd) <= 1e-4 * abs(fd) + 1e-7, (i, j, an, fd)

@@ -74,12 +74,12 @@ def test_instances_and_moments_match_oracle(O):
         assert np.abs(sigma2(mom[:, i]) / sigma2(want_mom) - 1).max() < 1e-5
 
 
-def test_modes_and_tiles_are_bitwise_identical():
+def test_modes_and_tiles_agree():
     chs, phis = channels()
     ref = None
-    for mode, tile, gsteps in [("persistent", 256, 16), ("per_step", 128, 16), ("persistent", 512, 7),
-                               ("per_step", 256, 1)]:
-        b = Batch(chs, mode=mode, tile_cols=tile, graph_steps=gsteps)
+    for mode, tile, gsteps in [("persistent", 16, 16), ("per_step", 8, 16), ("persistent", 5, 7),
+                               ("per_step", 32, 1)]:
+        b = Batch(chs, mode=mode, tile_rows=tile, graph_steps=gsteps)
         b.set_phi(phis)
         mom = b.run(53)
         phi = torch.cat([g.reshape(-1) for g in b.get_phi()]).cpu().numpy()
@@ -87,14 +87,17 @@ def test_modes_and_tiles_are_bitwise_identical():
         if ref is None:
             ref = (mom, phi)
         else:
-            assert np.array_equal(mom, ref[0]), (mode, tile)
+            # the fields are bitwise identical; the moment sums differ only in
+            # the summation order of the column sums over tile strips
             assert np.array_equal(phi, ref[1]), (mode, tile)
+            assert np.abs(mom[..., 0] / ref[0][..., 0] - 1).max() < 1e-7, (mode, tile)
+            assert np.abs(sigma2(mom) / sigma2(ref[0]) - 1).max() < 1e-7, (mode, tile)
     b = Batch(chs)
     b.set_phi(phis)
     b.autotune(steps=16)
     b.set_phi(phis)
     mom = b.run(53)
-    assert np.array_equal(mom, ref[0])
+    assert np.abs(sigma2(mom) / sigma2(ref[0]) - 1).max() < 1e-7
 
 
 def test_instance_equals_standalone_solver():

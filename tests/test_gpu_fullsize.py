@@ -68,3 +68,31 @@ def test_d3q15_384_windows(O):
         want = O.run(p, p0.astype(np.float64)[np.ix_(iz, iy, ix)].reshape(-1), nsteps, u=wu).reshape(n, n, n)
         c = slice(half - keep, half + keep + 1)
         assert rel_l2(got[np.ix_(iz, iy, ix)][c, c, c], want[c, c, c]) <= 1e-5
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16", 2e-3), ("bf16", 2e-3)])
+def test_vortex_5000_steps_error_vs_fp64(O, storage, tol):
+    """The configured length of the time-varying-velocity workload (5000 steps,
+    tau = 1, full anisotropic D, Gaussian hill, vortex u(x, t)) on a 256^2 grid that
+    the oracle finishes in seconds: relative L2 error of phi against FP64 stays
+    within the stated tolerance for every storage form."""
+    n, steps, tau = 256, 5000, 1.0
+    wl = W.vortex_workload(n, tau)
+    a = wl["a"].astype(np.float32)
+    sched = W.vortex_schedule(2000).astype(np.float32)
+    p0 = wl["phi0"].astype(np.float32)
+    s = Solver(nx=n, ny=n, storage=storage)
+    s.set_D(wl["D"])
+    s.set_velocity(torch.from_numpy(a).cuda(), torch.from_numpy(sched).cuda())
+    s.set_phi(torch.from_numpy(p0).cuda())
+    s.step(steps)
+    got = s.get_phi().cpu().numpy().astype(np.float64)
+    s.close()
+    p = O.Params(nx=n, ny=n, A=O.A_from_D(wl["D"]))
+    aa = a.astype(np.float64).reshape(2, -1)
+    sc = sched.astype(np.float64)
+    want = O.run(p, p0.astype(np.float64).reshape(-1), steps,
+                 u_of_t=lambda t: aa * sc[t % len(sc)][:, None]).reshape(n, n)
+    err = rel_l2(got, want)
+    print(f"{storage}: relative L2 error after {steps} steps = {err:.3e}")
+    assert err <= tol
