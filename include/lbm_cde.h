@@ -77,7 +77,9 @@ enum {
  * FP32 in every form. */
 enum {
     LBM_STORE_F32 = 0,      /* f'_i in FP32                                          */
-    LBM_STORE_F16_NEQ = 1,  /* g_i = f'_i - f^eq_i(phi, u) in FP16, phi in FP32     */
+    LBM_STORE_F16_NEQ = 1,  /* g_i = f'_i - f^eq_i(phi, u) in FP16, phi in FP32; g is
+                               stored times 2^11 (exact), so |g| must stay below 32
+                               (phi up to about 100); BF16 has FP32's range            */
     LBM_STORE_BF16_NEQ = 2  /* g_i in BF16, phi in FP32                              */
 };
 

@@ -252,15 +252,21 @@ template <> struct StT<ST_F32> { using T = float; };
 template <> struct StT<ST_F16> { using T = __half; };
 template <> struct StT<ST_BF16> { using T = __nv_bfloat16; };
 
+// FP16 offsets are stored multiplied by 2^11 (exact): the non-equilibrium
+// offsets of dilute regions (phi ~ 1e-4) then stay in FP16's normal range
+// instead of its subnormals, while |g| up to 32 remains representable.
+constexpr float F16_SCALE = 2048.0f;
+
 __device__ __forceinline__ float ldg_f(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldg_f(const __half* p) {
-    return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
+    return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p)))) *
+           (1.0f / F16_SCALE);
 }
 __device__ __forceinline__ float ldg_f(const __nv_bfloat16* p) {
     return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p))));
 }
 __device__ __forceinline__ void st_f(float* p, float v) { *p = v; }
-__device__ __forceinline__ void st_f(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void st_f(__half* p, float v) { *p = __float2half_rn(v * F16_SCALE); }
 __device__ __forceinline__ void st_f(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
 // Schedule multipliers s(k) (t mod sched_len), 1 when there is no schedule.

@@ -214,3 +214,58 @@ def test_taylor_aris_tables_3_4_reproduced_on_gpu():
             assert 0.9 < er / want < 2.2, (tau, Pe, m, er, want)
         else:
             assert abs(er - want) <= max(0.015 * want, 8e-4), (tau, Pe, m, er, want)
+
+
+def test_fig5_regions_on_gpu(O):
+    """Fig. 5 set-up (U = 0.1, W = 32, tau = 2 U W / Pe + 1/2) for the four models at
+    one Pe in each of the paper's three regions (Sec. 3.2): Pe = 16 (tau = 0.9):
+    MRT-A below MRT-B3; Pe = 30 (tau = 0.71): MRT-B3 a little below MRT-A;
+    Pe = 64 (tau = 0.6): MRT-A below MRT-B3 again; MRT-A below MRT-B1 and MRT-B2
+    throughout. The GPU errors equal the FP64 oracle's exact-moment values."""
+    W, nx, U = 32, 4096, 0.1
+    ny = W + 1
+    models = ["A", "B1", "B2", "B3"]
+    omodels = [O.MRT_A, O.MRT_B1, O.MRT_B2, O.MRT_B3]
+    pes = [16.0, 30.0, 64.0]
+    nsteps = 50000
+    u = poiseuille_row(ny, U)
+    cols = np.arange(nx)
+    pulse = ((cols / nx >= 0.197) & (cols / nx <= 0.203)).astype(np.float32)
+    chans, meta = [], []
+    for Pe in pes:
+        tau = 2 * U * W / Pe + 0.5
+        alpha = (tau - 0.5) / 3
+        for m in models:
+            chans.append({"nx": nx, "ny": ny, "D": np.eye(2) * alpha, "u_row": u, "model": m, "tie": False,
+                          "s": [1.0, 1.1, 1.1, None, 1 / tau, None, 1 / tau, 1.2, 1.2],
+                          "x_ref0": 0.2 * nx, "x_ref_velocity": mean_velocity(u)})
+            meta.append((Pe, tau, alpha, m))
+    b = Batch(chans, graph_steps=500)
+    b.set_phi([np.broadcast_to(pulse, (ny, nx)).copy() for _ in chans])
+    mom = b.run(nsteps)
+    b.close()
+    er_gpu, er_or = {}, {}
+    wy = np.ones(ny)
+    wy[0] = wy[-1] = 0.5
+    for i, (Pe, tau, alpha, m) in enumerate(meta):
+        s2 = sigma2(mom[:, i])
+        a_gpu = (s2[-1] - s2[-2001]) / 4000.0
+        a_an = alpha * (1 + Pe * Pe / 210.0)
+        er_gpu[(Pe, m)] = abs(a_gpu - a_an) / a_an * 100
+        p = O.Params(q=9, model=omodels[models.index(m)], nx=1, ny=ny, bc_lo=O.NOFLUX_NODE,
+                     bc_hi=O.NOFLUX_NODE, A=np.eye(2) / tau,
+                     s=np.array([1.0, 1.1, 1.1, 0, 1 / tau, 0, 1 / tau, 1.2, 1.2]), tie=False)
+        _, _, Mi, _ = O.tables(p)
+        F0 = np.zeros((3, 9, ny))
+        for yy in range(ny):
+            F0[0, :, yy] = Mi @ O.meq(p, 1.0, [float(u[0, yy]), 0.0])
+        so = O.variance_from_moments(O.channel_moments(p, u[0].astype(np.float64), F0, wy, nsteps))
+        a_or = (so[-1] - so[-2001]) / 4000.0
+        er_or[(Pe, m)] = abs(a_or - a_an) / a_an * 100
+        assert abs(er_gpu[(Pe, m)] - er_or[(Pe, m)]) <= 1e-3 + 2e-3 * er_or[(Pe, m)], (Pe, m)
+    e = er_gpu
+    for Pe in pes:
+        assert e[(Pe, "A")] < e[(Pe, "B1")] < e[(Pe, "B2")]
+    assert e[(16.0, "A")] < e[(16.0, "B3")]
+    assert e[(30.0, "B3")] < e[(30.0, "A")]
+    assert e[(64.0, "A")] < e[(64.0, "B3")]
