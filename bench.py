@@ -160,15 +160,20 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def replica_totals(seconds, units, world):
+    """Replicas: (max time over ranks, units summed over ranks). The only
+    cross-rank traffic of the benchmark (the path itself has no collective)."""
     if world == 1:
-        return x
+        return seconds, units
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def make_solver(store: str):
@@ -438,13 +443,14 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
+    if args.impl == "reference":
+        # the FP64 oracle on the host cores: rank 0 alone runs and prints
+        run_reference(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
+        return
+
     import torch
 
     rank, world, local = dist_init(args)
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        barrier(world)
-        return
 
     import paper_1404_2363_gb300 as P
 
@@ -461,10 +467,10 @@ def main():
         t_wall1 = time.time()
         time.sleep(0.25)
     barrier(world)
-    dt_max = max_over_ranks(dt, world)
+    dt_max, units = replica_totals(dt, ncell * args.steps, world)
     mass_ok = s.sum_phi()
     s.close()
-    value = world * ncell * args.steps / dt_max / 1e6
+    value = units / dt_max / 1e6
     avg_launch = dt / args.steps
     peak, peak_kind = peaks()
     achieved = ncell * B_LU[store] / avg_launch / 1e9
