@@ -166,13 +166,15 @@ lbm_status lbm_cde_set_phi(lbm_cde_t h, const float* phi_dev);
 lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps);
 
 /* Sets the launch shape of the step kernel: block threads per CTA along x
- * (a multiple of 32 in [32, 256]) and vec cells per thread (1 or 2; 3 selects
- * the row-walking kernel of the D2Q9 16-bit storage forms). Results do not
- * depend on the shape. Errors: LBM_E_ARG. */
+ * (a multiple of 32 in [32, 256]) and vec cells per thread (1 or 2; for the
+ * D2Q9 16-bit storage forms, 3 selects the row-walking kernel and 4 the
+ * shared-memory tile kernel, which needs nx % 32 == 0 and ny % 8 == 0).
+ * Results do not depend on the shape beyond FP32 rounding order. Errors:
+ * LBM_E_ARG. */
 lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec);
 
 /* Autotuner: times every launch shape (block 64/128/256 x vec 1/2, and the
- * row-walking kernel for D2Q9 16-bit storage) over `steps` steps from the
+ * row-walking and tile kernels for D2Q9 16-bit storage) over `steps` steps from the
  * current state, keeps the fastest, and restores the state and step count.
  * With LBMCDE_TUNE_CACHE set, the choice is read from / appended to that text
  * file (lines "key block vec"; the key holds lattice, storage, grid, velocity

@@ -441,10 +441,12 @@ lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps)
 lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec)
 {
     if (!h) return fail(h, LBM_E_ARG, "NULL handle");
-    if (block < 32 || block > 256 || block % 32 != 0 || vec < 1 || vec > 3 ||
-        (vec == 3 && !(h->q == 9 && h->neq)))
+    const bool tile_ok = h->d.nx % 32 == 0 && h->d.ny % 8 == 0;
+    if (block < 32 || block > 256 || block % 32 != 0 || vec < 1 || vec > 4 ||
+        (vec >= 3 && !(h->q == 9 && h->neq)) || (vec == 4 && !tile_ok))
         return fail(h, LBM_E_ARG, "block must be a multiple of 32 in [32, 256]; vec 1 or 2 "
-                                  "(3: row-walking kernel, D2Q9 16-bit storage only)");
+                                  "(3: row-walking kernel, 4: shared-memory tile kernel with nx % 32 == 0 "
+                                  "and ny % 8 == 0; both D2Q9 16-bit storage only)");
     h->cfg.block = block;
     h->cfg.vec = vec;
     return LBM_OK;
@@ -528,10 +530,10 @@ lbm_status lbm_cde_autotune(lbm_cde_t h, int64_t steps, int32_t* block_out, int3
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int blocks[3] = {64, 128, 256};
-    const int maxvec = (h->q == 9 && h->neq) ? 3 : 2;
+    const int maxvec = (h->q == 9 && h->neq) ? (h->d.nx % 32 == 0 && h->d.ny % 8 == 0 ? 4 : 3) : 2;
     for (int vec = 1; vec <= maxvec && s == LBM_OK; ++vec)
         for (int bi = 0; bi < 3 && s == LBM_OK; ++bi) {
-            if (vec == 3 && bi > 0) break;          // the row-walking kernel has one shape
+            if (vec >= 3 && bi > 0) break;          // the row-walking and tile kernels have one shape
             h->cfg = LaunchCfg{blocks[bi], vec};
             s = lbm_cde_set_state(h, save, t0);
             if (s == LBM_OK) s = lbm_cde_step(h, 2);     // warm

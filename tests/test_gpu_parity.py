@@ -116,12 +116,27 @@ def test_row_walking_offset_kernel(O, storage, bc, ukind):
     assert rel_l2(got, want) <= TOL[storage]
 
 
-def _run_vec3(case, phi0, a, sched):
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("bc,ukind", [(("periodic", "periodic"), "field"), (("noflux", "noflux"), "row"),
+                                      (("bounceback", "bounceback"), "field"),
+                                      (("dirichlet", "dirichlet"), "field"), (("periodic", "periodic"), "none")])
+def test_tile_offset_kernel(O, storage, bc, ukind):
+    """The shared-memory tile kernel of the 16-bit forms (launch vec = 4) against
+    the oracle on a 320 x 40 grid (whole 32 x 8 tiles, several in each direction)."""
+    case = Case(storage=storage, bc=bc, ukind=ukind, sched=ukind != "none", nx=320, ny=40,
+                phi_w=(1.0, 0.25) if bc[0] == "dirichlet" else (0.0, 0.0))
+    phi0, a, sched = case.inputs()
+    got, _ = _run_vec3(case, phi0, a, sched, vec=4)
+    want = run_oracle(O, case, phi0, a, sched)
+    assert rel_l2(got, want) <= TOL[storage]
+
+
+def _run_vec3(case, phi0, a, sched, vec=3):
     import torch
     from paper_1404_2363_gb300.solver import Solver
 
     s = Solver(nx=case.nx, ny=case.ny, storage=case.storage, bc=case.bc, phi_w=case.phi_w)
-    s.set_launch(256, 3)
+    s.set_launch(256, vec)
     s.set_D(case.D)
     if a is not None:
         s.set_velocity(torch.from_numpy(a).cuda(), None if sched is None else torch.from_numpy(sched).cuda(),
