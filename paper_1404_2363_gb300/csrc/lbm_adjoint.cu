@@ -26,7 +26,7 @@ __host__ __device__ constexpr int ngrad() { return 2 * L::DIM * L::DIM + L::Q; }
 constexpr int ADJ_ROWS = 8;
 
 template <class L, int UK, bool WALLS>
-__global__ void __launch_bounds__(256, 3) k_adjoint(const AdjArgs a)
+__global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArgs a)
 {
     constexpr int Q = L::Q, DIM = L::DIM, NG = ngrad<L>();
     const int nx = a.nx, ny = a.ny, nz = a.nz;

@@ -29,6 +29,7 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="run N Taylor-Aris channels (per-step mode) instead")
     ap.add_argument("--tile", type=int, default=16, help="rows per batch warp tile")
     ap.add_argument("--mode", default="per_step", choices=["per_step", "persistent"])
+    ap.add_argument("--adjoint", action="store_true", help="forward_ckpt + backward (dL/dD, dL/da)")
     args = ap.parse_args()
     if args.batch:
         return run_batch(args)
@@ -48,6 +49,12 @@ def main():
         a = torch.from_numpy(g.uniform(-0.05, 0.05, (dim,) + shape).astype(np.float32)).cuda()
         s.set_velocity(a)
     phi0 = torch.from_numpy((0.5 + g.random(shape)).astype(np.float32)).cuda()
+    if args.adjoint:
+        s.forward_ckpt(phi0, args.steps)
+        _, dD, _, _ = s.backward(torch.ones(shape, device="cuda"), want_da=args.ukind == "field")
+        s.close()
+        print(f"ok adjoint n={n} steps={args.steps} dL/dD[0,0]={dD[0, 0]:.6e}")
+        return
     s.set_phi(phi0)
     s.step(args.steps)
     m = s.sum_phi()
