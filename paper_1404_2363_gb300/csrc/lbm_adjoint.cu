@@ -50,14 +50,16 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
     for (int y = y0; y < y0 + ADJ_ROWS && y < ny; ++y) {
         const int ys[3] = {y + 1 == ny ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};
         const long long cell = (long long)xc + (long long)nx * (y + (long long)ny * z);
+        // pull source of population i = push target of its adjoint (recomputed
+        // where used rather than held in 64-bit registers through the step)
+        auto tgt = [&](int i) -> long long {
+            return (long long)xs[L::ex(i) + 1] + (long long)nx * (ys[L::ey(i) + 1] + (long long)ny * zs[L::ez(i) + 1]);
+        };
         float mu[Q], f[Q];
-        long long tgt[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            tgt[i] = (long long)xs[L::ex(i) + 1] +
-                     (long long)nx * (ys[L::ey(i) + 1] + (long long)ny * zs[L::ez(i) + 1]);
             mu[i] = __ldg(a.mu_in + (long long)i * N + cell);
-            f[i] = __ldg(a.fprev + (long long)i * N + tgt[i]);
+            f[i] = __ldg(a.fprev + (long long)i * N + tgt(i));
         }
         const bool lo = WALLS && y == 0 && a.bc_lo != BC_PERIODIC;
         const bool hi = WALLS && y == ny - 1 && a.bc_hi != BC_PERIODIC;
@@ -76,18 +78,7 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
 
         // forward non-equilibrium moments d = M f - m^eq(phi, u(k))
         float m[Q];
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            float acc = 0.f;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int w = L::M(k, i);
-                if (w == 1) acc += f[i];
-                else if (w == -1) acc -= f[i];
-                else if (w != 0) acc = fmaf((float)w, f[i], acc);
-            }
-            m[k] = acc;
-        }
+        for (int k = 0; k < Q; ++k) m[k] = int_dot<Q>([k](int i) { return L::M(k, i); }, f);
         const float phi = m[0];
         float v[Q];
 #pragma unroll
@@ -107,18 +98,9 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
 
         // a = M^-T mu = diag(1/|M_r|^2) M mu
         float av[Q];
+        for (int k = 0; k < Q; ++k) av[k] = int_dot<Q>([k](int i) { return L::M(k, i); }, mu);
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            float acc = 0.f;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int w = L::M(k, i);
-                if (w == 1) acc += mu[i];
-                else if (w == -1) acc -= mu[i];
-                else if (w != 0) acc = fmaf((float)w, mu[i], acc);
-            }
-            av[k] = acc * (1.0f / (float)row_norm2<L>(k));
-        }
+        for (int k = 0; k < Q; ++k) av[k] *= 1.0f / (float)row_norm2<L>(k);
         // b = S^T a (S of Eq. 31 / A.5: diagonal rates, flux block A, couplings C)
         float b[Q];
 #pragma unroll
@@ -142,18 +124,7 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
         for (int k = 0; k < Q; ++k) cv[k] = av[k] - b[k];
         cv[0] += vb;
         float nu[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            float acc = 0.f;
-#pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                const int w = L::M(k, i);
-                if (w == 1) acc += cv[k];
-                else if (w == -1) acc -= cv[k];
-                else if (w != 0) acc = fmaf((float)w, cv[k], acc);
-            }
-            nu[i] = acc;
-        }
+        for (int i = 0; i < Q; ++i) nu[i] = int_dot<Q>([i](int k) { return L::M(k, i); }, cv);
         if (!live) continue;
 
         // velocity partials: u(x, k) = a(x) s(k)  =>  dL/da += s(k) dL/du(k)
@@ -189,11 +160,11 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
             for (int i = 0; i < Q; ++i) {
                 if (L::ey(i) != 0 && ((L::ey(i) == 1) == lo)) continue;
                 if (kind == BC_NOFLUX && L::ey(i) != 0) out[(long long)i * N + cell] = 0.f;  // left the domain
-                out[(long long)i * N + tgt[i]] = nu[i];
+                out[(long long)i * N + tgt(i)] = nu[i];
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) out[(long long)i * N + tgt[i]] = nu[i];
+            for (int i = 0; i < Q; ++i) out[(long long)i * N + tgt(i)] = nu[i];
         }
     }
 

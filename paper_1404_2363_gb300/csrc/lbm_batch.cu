@@ -125,10 +125,7 @@ __device__ __forceinline__ void warp_tile(const BatchArgs& a, long long t, long 
             ux = __ldg(I.urow + y);
             uy = __ldg(I.urow + ny + y);
         }
-        float phi = 0.f;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) phi += f[i];
-        collide<D2Q9>(f, ux, uy, 0.f, cs);
+        const float phi = collide<D2Q9>(f, ux, uy, 0.f, cs);
         if (live) {
             const long long cell = base + (long long)y * nx + x;
 #pragma unroll
@@ -298,10 +295,7 @@ __global__ void __launch_bounds__(256) k_batch_step_cells(const BatchArgs a)
             ux = __ldg(I.urow + y);
             uy = __ldg(I.urow + ny + y);
         }
-        float phi = 0.f;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) phi += f[i];
-        collide<D2Q9>(f, ux, uy, 0.f, cs);
+        const float phi = collide<D2Q9>(f, ux, uy, 0.f, cs);
         if (live) {
             const long long cell = base + (long long)y * nx + x;
 #pragma unroll

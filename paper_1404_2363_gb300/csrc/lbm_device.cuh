@@ -190,40 +190,115 @@ __device__ __forceinline__ float int_dot(Wf W, const float* v)
 }
 
 // ---------------------------------------------------------------------------
-// Collision in moment space for one node (Eq. 11, 13 with Eq. 31 / A.5, 14).
+// The integer maps m = M v and v = M^T a. For D2Q9 both are evaluated as
+// sums and differences of the populations that share |e| (24 operations each
+// instead of the 50-58 of the row-by-row chains); D3Q15 uses the row chains.
 // ---------------------------------------------------------------------------
 template <class L>
-__device__ __forceinline__ void collide(float (&f)[L::Q], float ux, float uy, float uz,
-                                        const Coef& c)
+__device__ __forceinline__ void moments(const float (&v)[L::Q], float (&m)[L::Q])
+{
+    if constexpr (L::Q == 9) {
+        // axis pairs (1,3), (2,4) and diagonal pairs (5,7), (6,8) of Eq. 2
+        const float sx = v[1] + v[3], ax = v[1] - v[3];
+        const float sy = v[2] + v[4], ay = v[2] - v[4];
+        const float p57 = v[5] + v[7], d57 = v[5] - v[7];
+        const float p68 = v[6] + v[8], d68 = v[6] - v[8];
+        const float sa = sx + sy, sd = p57 + p68;      // |e| = 1 and |e|^2 = 2 sums
+        const float jx = d57 - d68, jy = d57 + d68;    // diagonal e_x and e_y sums
+        m[0] = v[0] + sa + sd;
+        m[1] = fmaf(2.f, sd, fmaf(-4.f, v[0], -sa));   // -4, -1, 2
+        m[2] = fmaf(-2.f, sa, fmaf(4.f, v[0], sd));    //  4, -2, 1
+        m[3] = ax + jx;
+        m[4] = fmaf(-2.f, ax, jx);
+        m[5] = ay + jy;
+        m[6] = fmaf(-2.f, ay, jy);
+        m[7] = sx - sy;
+        m[8] = p57 - p68;
+    } else {
+#pragma unroll
+        for (int k = 0; k < L::Q; ++k) m[k] = int_dot<L::Q>([k](int i) { return L::M(k, i); }, v);
+    }
+}
+
+// v_i = (M^T a)_i for i >= 1 (and i = 0 when FULL); a_0 is taken as zero when
+// ZERO0. Returns the sum of v_1 .. v_{Q-1} in a form that is exact in exact
+// arithmetic (D2Q9: 4 (A + B), see below), for the mass-balance closure.
+template <class L, bool ZERO0, bool FULL>
+__device__ __forceinline__ float populations(const float (&a)[L::Q], float (&v)[L::Q])
+{
+    if constexpr (L::Q == 9) {
+        // axis: v = A +- X + P (x) or A +- Y - P (y); diagonal: B +- Xd +- Yd +- R
+        const float A = ZERO0 ? fmaf(-2.f, a[2], -a[1]) : fmaf(-2.f, a[2], a[0] - a[1]);
+        const float B = ZERO0 ? fmaf(2.f, a[1], a[2]) : fmaf(2.f, a[1], a[0] + a[2]);
+        const float X = fmaf(-2.f, a[4], a[3]), Y = fmaf(-2.f, a[6], a[5]);
+        const float Xd = a[3] + a[4], Yd = a[5] + a[6];
+        const float AP = A + a[7], AM = A - a[7];
+        const float BP = B + a[8], BM = B - a[8];
+        const float XY = Xd + Yd, XmY = Xd - Yd;
+        v[1] = AP + X;
+        v[3] = AP - X;
+        v[2] = AM + Y;
+        v[4] = AM - Y;
+        v[5] = BP + XY;
+        v[7] = BP - XY;
+        v[6] = BM - XmY;
+        v[8] = BM + XmY;
+        if (FULL) v[0] = ZERO0 ? 4.f * (a[2] - a[1]) : fmaf(4.f, a[2], fmaf(-4.f, a[1], a[0]));
+        return 4.f * (A + B);
+    } else {
+        float sum = 0.f;
+#pragma unroll
+        for (int i = 1; i < L::Q; ++i) {
+            v[i] = int_dot<L::Q>([i](int k) { return (ZERO0 && k == 0) ? 0 : L::M(k, i); }, a);
+            sum += v[i];
+        }
+        if (FULL) v[0] = int_dot<L::Q>([](int k) { return (ZERO0 && k == 0) ? 0 : L::M(k, 0); }, a);
+        return sum;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Collision in moment space for one node (Eq. 11, 13 with Eq. 31 / A.5, 14).
+// On return f holds the post-collision populations f' (OFFSET = false) or
+// their offsets from the linear equilibrium, g_i = f'_i - phi (w_i + k_i e_i.u)
+// (OFFSET = true, the 16-bit storage forms), computed in moment space as
+// g = M^-1 (m' - m^eq_lin). Returns phi = m_0.
+// ---------------------------------------------------------------------------
+template <class L, bool OFFSET = false>
+__device__ __forceinline__ float collide(float (&f)[L::Q], float ux, float uy, float uz,
+                                         const Coef& c)
 {
     constexpr int Q = L::Q;
     float m[Q];
-#pragma unroll
-    for (int k = 0; k < Q; ++k) m[k] = int_dot<Q>([k](int i) { return L::M(k, i); }, f);
+    moments<L>(f, m);
     const float phi = m[0];
     const float u[3] = {ux, uy, uz};
-    // non-equilibrium parts d = m - m^eq (Eq. 15 / A.3 with c1 = 1, c2 from Eq. 16 / A.4)
-    float d[Q];
+    // dl = m - m^eq_lin (Eq. 15 / A.3 with c1 = 1, c2 from Eq. 16 / A.4: linear in u);
+    // d = dl - (u^2 terms of the MRT-B1/B2 equilibria, zero otherwise)
+    float dl[Q], d[Q];
     const float u2 = ux * ux + uy * uy + uz * uz;
-    d[0] = 0.f;
-    d[1] = m[1] - fmaf(c.b1, u2, c.meq1) * phi;
-    d[2] = m[2] - fmaf(c.b2, u2, c.meq2) * phi;
+    dl[0] = d[0] = 0.f;
+    dl[1] = fmaf(-c.meq1, phi, m[1]);
+    dl[2] = fmaf(-c.meq2, phi, m[2]);
+    d[1] = fmaf(-c.b1 * u2, phi, dl[1]);
+    d[2] = fmaf(-c.b2 * u2, phi, dl[2]);
 #pragma unroll
     for (int a = 0; a < L::DIM; ++a) {
-        d[3 + 2 * a] = m[3 + 2 * a] - phi * u[a];
-        d[4 + 2 * a] = m[4 + 2 * a] + phi * u[a];
+        d[3 + 2 * a] = dl[3 + 2 * a] = fmaf(-phi, u[a], m[3 + 2 * a]);
+        d[4 + 2 * a] = dl[4 + 2 * a] = fmaf(phi, u[a], m[4 + 2 * a]);
     }
 #pragma unroll
-    for (int k = 3 + 2 * L::DIM; k < Q; ++k) d[k] = m[k];
-    if (L::Q == 9) {   // MRT-B1/B2 second-order terms (zero coefficients otherwise)
-        d[7] -= c.g7 * (ux * ux - uy * uy) * phi;
-        d[8] -= c.g8 * (ux * uy) * phi;
+    for (int k = 3 + 2 * L::DIM; k < Q; ++k) d[k] = dl[k] = m[k];
+    if (L::Q == 9) {
+        d[7] = fmaf(-c.g7 * (ux * ux - uy * uy), phi, dl[7]);
+        d[8] = fmaf(-c.g8 * (ux * uy), phi, dl[8]);
     }
-    // relaxation m' = m - S d
+    // relaxation m' = m - S d; the offset form keeps m' - m^eq_lin = dl - S d
+    const float (&base)[Q] = OFFSET ? dl : m;
     float mp[Q];
-    mp[0] = m[0];
-    mp[1] = fmaf(-c.s[1], d[1], m[1]);
-    mp[2] = fmaf(-c.s[2], d[2], m[2]);
+    mp[0] = OFFSET ? 0.f : phi;
+    mp[1] = fmaf(-c.s[1], d[1], base[1]);
+    mp[2] = fmaf(-c.s[2], d[2], base[2]);
 #pragma unroll
     for (int a = 0; a < L::DIM; ++a) {
         float r = 0.f;
@@ -232,25 +307,21 @@ __device__ __forceinline__ void collide(float (&f)[L::Q], float ux, float uy, fl
             r = fmaf(c.A[a * L::DIM + b], d[3 + 2 * b], r);
             r = fmaf(c.C[a * L::DIM + b], d[4 + 2 * b], r);
         }
-        mp[3 + 2 * a] = m[3 + 2 * a] - r;
-        mp[4 + 2 * a] = fmaf(-c.s[4 + 2 * a], d[4 + 2 * a], m[4 + 2 * a]);
+        mp[3 + 2 * a] = base[3 + 2 * a] - r;
+        mp[4 + 2 * a] = fmaf(-c.s[4 + 2 * a], d[4 + 2 * a], base[4 + 2 * a]);
     }
 #pragma unroll
-    for (int k = 3 + 2 * L::DIM; k < Q; ++k) mp[k] = fmaf(-c.s[k], d[k], m[k]);
+    for (int k = 3 + 2 * L::DIM; k < Q; ++k) mp[k] = fmaf(-c.s[k], d[k], base[k]);
     // f' = M^T diag(1 / |row|^2) m'
 #pragma unroll
     for (int k = 0; k < Q; ++k) mp[k] *= 1.0f / (float)row_norm2<L>(k);
-    float rest = phi;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const float acc = int_dot<Q>([i](int k) { return L::M(k, i); }, mp);
-        f[i] = acc;
-        rest -= acc;
-    }
+    const float moving = populations<L, OFFSET, false>(mp, f);
     // The rest population closes the mass balance: sum_i f'_i = m'_0 = phi
-    // (row 0 of M^-1 m'). Taking it as phi minus the moving populations keeps
-    // FP32 rounding of the 1/|M_0|^2 factor from biasing the total mass.
-    f[0] = rest;
+    // (row 0 of M^-1 m'), and sum_i g_i = 0. Taking it from the moving
+    // populations keeps FP32 rounding of the 1/|M_0|^2 factor from biasing
+    // the total mass.
+    f[0] = OFFSET ? -moving : phi - moving;
+    return phi;
 }
 
 // ---------------------------------------------------------------------------
@@ -428,19 +499,10 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
         }
         float ux, uy, uz;
         vel_ix<UK, L::DIM, IX>(a, N, cell[j], y, s_now, ux, uy, uz);
-        float phi = 0.f;
-        if (NEQ) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) phi += f[j][i];
-        }
-        collide<L>(f[j], ux, uy, uz, a.c);
+        const float phi = collide<L, NEQ>(f[j], ux, uy, uz, a.c);
         if (!live[j]) continue;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            float v = f[j][i];
-            if (NEQ) v -= phi * feq_unit<L>(a.c, i, ux, uy, uz);
-            st_f(dst + (IX)i * N + cell[j], v);
-        }
+        for (int i = 0; i < Q; ++i) st_f(dst + (IX)i * N + cell[j], f[j][i]);
         if (NEQ) a.phi_dst[cell[j]] = phi;
     }
 }
@@ -599,14 +661,10 @@ __global__ void __launch_bounds__(256) k_step_neq_d2q9(const StepArgs a)
             }
         }
         const float ux = AX[1] * s_now[0], uy = AY[1] * s_now[1];
-        float phi = 0.f;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) phi += f[i];
-        collide<L>(f, ux, uy, 0.f, c);
+        const float phi = collide<L, true>(f, ux, uy, 0.f, c);
         if (live) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i)
-                st_f(dst + (long long)i * N + cell, f[i] - phi * feq_unit<L>(c, i, ux, uy, 0.f));
+            for (int i = 0; i < 9; ++i) st_f(dst + (long long)i * N + cell, f[i]);
             a.phi_dst[cell] = phi;
         }
         if (more) {
@@ -753,12 +811,9 @@ __global__ void __launch_bounds__(256) k_step_neq_tile_d2q9(const StepArgs a)
         }
     }
     const float ux = axo * s_now[0], uy = ayo * s_now[1];
-    float phi = 0.f;
+    const float phi = collide<L, true>(f, ux, uy, 0.f, c);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) phi += f[i];
-    collide<L>(f, ux, uy, 0.f, c);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) st_f(dst + i * N + cell, f[i] - phi * feq_unit<L>(c, i, ux, uy, 0.f));
+    for (int i = 0; i < 9; ++i) st_f(dst + i * N + cell, f[i]);
     a.phi_dst[cell] = phi;
 }
 
