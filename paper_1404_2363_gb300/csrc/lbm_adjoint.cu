@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
 
         // forward non-equilibrium moments d = M f - m^eq(phi, u(k))
         float m[Q];
+#pragma unroll
         for (int k = 0; k < Q; ++k) m[k] = int_dot<Q>([k](int i) { return L::M(k, i); }, f);
         const float phi = m[0];
         float v[Q];
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
 
         // a = M^-T mu = diag(1/|M_r|^2) M mu
         float av[Q];
+#pragma unroll
         for (int k = 0; k < Q; ++k) av[k] = int_dot<Q>([k](int i) { return L::M(k, i); }, mu);
 #pragma unroll
         for (int k = 0; k < Q; ++k) av[k] *= 1.0f / (float)row_norm2<L>(k);
@@ -124,6 +126,7 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
         for (int k = 0; k < Q; ++k) cv[k] = av[k] - b[k];
         cv[0] += vb;
         float nu[Q];
+#pragma unroll
         for (int i = 0; i < Q; ++i) nu[i] = int_dot<Q>([i](int k) { return L::M(k, i); }, cv);
         if (!live) continue;
 
