@@ -153,7 +153,8 @@ lbm_status lbm_cde_get_rates(lbm_cde_t h, double* A_out, double* s_out);
  *   a_dev    : device FP32, [dim][ncell] (FIELD) or [dim][ny] (ROW_PROFILE);
  *              borrowed until the next set_velocity or destroy
  *   sched_dev: device FP32 [sched_len][dim] per-component multipliers s(t),
- *              indexed by t mod sched_len; NULL means s = 1
+ *              indexed by t mod sched_len (1 <= sched_len <= 2^26); NULL
+ *              means s = 1; borrowed like a_dev
  * Errors: LBM_E_ARG. */
 lbm_status lbm_cde_set_velocity(lbm_cde_t h, int32_t kind, const float* a_dev,
                                 const float* sched_dev, int64_t sched_len);
@@ -167,14 +168,16 @@ lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps);
 
 /* Sets the launch shape of the step kernel: block threads per CTA along x
  * (a multiple of 32 in [32, 256]) and vec cells per thread (1 or 2; for the
- * D2Q9 16-bit storage forms, 3 selects the row-walking kernel and 4 the
- * shared-memory tile kernel, which needs nx % 32 == 0 and ny % 8 == 0).
+ * D2Q9 16-bit storage forms, 3 selects the row-walking kernel, 4 the
+ * shared-memory tile kernel, which needs nx % 32 == 0 and ny % 8 == 0, and 5
+ * the node-pair kernel (two adjacent nodes per thread in paired FP32
+ * arithmetic), which needs nx even and 12 ncell < 2^31).
  * Results do not depend on the shape beyond FP32 rounding order. Errors:
  * LBM_E_ARG. */
 lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec);
 
 /* Autotuner: times every launch shape (block 64/128/256 x vec 1/2, and the
- * row-walking and tile kernels for D2Q9 16-bit storage) over `steps` steps from the
+ * row-walking, tile and node-pair kernels for D2Q9 16-bit storage) over `steps` steps from the
  * current state, keeps the fastest, and restores the state and step count.
  * With LBMCDE_TUNE_CACHE set, the choice is read from / appended to that text
  * file (lines "key block vec"; the key holds lattice, storage, grid, velocity

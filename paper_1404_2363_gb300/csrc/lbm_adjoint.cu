@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
     const int zs[3] = {z + 1 == nz ? 0 : z + 1, z, z == 0 ? nz - 1 : z - 1};
     const Coef& c = a.c;
     float s_now[3];
-    sched_at(a.sched, a.sched_len, a.k, DIM, s_now);
+    sched_row_at(a.sched, a.srow, DIM, s_now);
 
     float g[NG];
 #pragma unroll

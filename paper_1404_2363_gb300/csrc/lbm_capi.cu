@@ -208,7 +208,7 @@ static StepArgs make_args(lbm_cde_t h, int src_idx)
     a.ua = h->ua;
     a.sched = h->sched;
     a.sched_len = h->sched_len;
-    a.k = h->t + 1;
+    set_step(a, h->t + 1);
     a.nx = (int)h->d.nx;
     a.ny = (int)h->d.ny;
     a.nz = (int)h->d.nz;
@@ -401,7 +401,8 @@ lbm_status lbm_cde_set_velocity(lbm_cde_t h, int32_t kind, const float* a_dev, c
     if (kind != LBM_U_NONE && kind != LBM_U_FIELD && kind != LBM_U_ROW_PROFILE)
         return fail(h, LBM_E_ARG, "bad velocity kind");
     if (kind != LBM_U_NONE && !a_dev) return fail(h, LBM_E_ARG, "velocity pointer is NULL");
-    if (sched_dev && sched_len <= 0) return fail(h, LBM_E_ARG, "sched_len must be > 0");
+    if (sched_dev && (sched_len <= 0 || sched_len > (1LL << 26)))
+        return fail(h, LBM_E_ARG, "sched_len must be in [1, 2^26]");
     h->ukind = kind;
     h->ua = kind == LBM_U_NONE ? nullptr : a_dev;
     h->sched = sched_dev;
@@ -442,11 +443,13 @@ lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec)
 {
     if (!h) return fail(h, LBM_E_ARG, "NULL handle");
     const bool tile_ok = h->d.nx % 32 == 0 && h->d.ny % 8 == 0;
-    if (block < 32 || block > 256 || block % 32 != 0 || vec < 1 || vec > 4 ||
-        (vec >= 3 && !(h->q == 9 && h->neq)) || (vec == 4 && !tile_ok))
+    const bool pair_ok = h->d.nx % 2 == 0 && 12LL * h->ncell < (1LL << 31);
+    if (block < 32 || block > 256 || block % 32 != 0 || vec < 1 || vec > 5 ||
+        (vec >= 3 && !(h->q == 9 && h->neq)) || (vec == 4 && !tile_ok) || (vec == 5 && !pair_ok))
         return fail(h, LBM_E_ARG, "block must be a multiple of 32 in [32, 256]; vec 1 or 2 "
                                   "(3: row-walking kernel, 4: shared-memory tile kernel with nx % 32 == 0 "
-                                  "and ny % 8 == 0; both D2Q9 16-bit storage only)");
+                                  "and ny % 8 == 0, 5: node-pair kernel with nx even; 3-5 D2Q9 16-bit "
+                                  "storage only)");
     h->cfg.block = block;
     h->cfg.vec = vec;
     return LBM_OK;
@@ -529,25 +532,33 @@ lbm_status lbm_cde_autotune(lbm_cde_t h, int64_t steps, int32_t* block_out, int3
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int blocks[3] = {64, 128, 256};
-    const int maxvec = (h->q == 9 && h->neq) ? (h->d.nx % 32 == 0 && h->d.ny % 8 == 0 ? 4 : 3) : 2;
-    for (int vec = 1; vec <= maxvec && s == LBM_OK; ++vec)
-        for (int bi = 0; bi < 3 && s == LBM_OK; ++bi) {
-            if (vec >= 3 && bi > 0) break;          // the row-walking and tile kernels have one shape
-            h->cfg = LaunchCfg{blocks[bi], vec};
-            s = lbm_cde_set_state(h, save, t0);
-            if (s == LBM_OK) s = lbm_cde_step(h, 2);     // warm
-            cudaEventRecord(e0, h->st);
-            if (s == LBM_OK) s = lbm_cde_step(h, steps);
-            cudaEventRecord(e1, h->st);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (s == LBM_OK && ms < best) {
-                best = ms;
-                best_cfg = h->cfg;
-            }
+    // candidates: generic kernel (1 or 2 nodes per thread) at 64/128/256 threads;
+    // for D2Q9 16-bit storage also the row-walking and tile kernels (one shape
+    // each) and the node-pair kernel at 64/128/256 threads
+    std::vector<LaunchCfg> cand;
+    for (int vec = 1; vec <= 2; ++vec)
+        for (int b : {64, 128, 256}) cand.push_back(LaunchCfg{b, vec});
+    if (h->q == 9 && h->neq) {
+        cand.push_back(LaunchCfg{256, 3});
+        if (h->d.nx % 32 == 0 && h->d.ny % 8 == 0) cand.push_back(LaunchCfg{256, 4});
+        if (h->d.nx % 2 == 0 && 12LL * h->ncell < (1LL << 31))
+            for (int b : {64, 128, 256}) cand.push_back(LaunchCfg{b, 5});
+    }
+    for (size_t ci = 0; ci < cand.size() && s == LBM_OK; ++ci) {
+        h->cfg = cand[ci];
+        s = lbm_cde_set_state(h, save, t0);
+        if (s == LBM_OK) s = lbm_cde_step(h, 2);     // warm
+        cudaEventRecord(e0, h->st);
+        if (s == LBM_OK) s = lbm_cde_step(h, steps);
+        cudaEventRecord(e1, h->st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (s == LBM_OK && ms < best) {
+            best = ms;
+            best_cfg = h->cfg;
         }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->cfg = s == LBM_OK ? best_cfg : keep;
@@ -698,6 +709,7 @@ static lbm::AdjArgs make_adj(lbm_cde_t h, int64_t k, const float* mu_in, float* 
     a.sched = h->sched;
     a.sched_len = h->sched_len;
     a.k = k;
+    a.srow = lbm::sched_row(k, h->sched ? h->sched_len : 0);
     a.nx = (int)h->d.nx;
     a.ny = (int)h->d.ny;
     a.nz = (int)h->d.nz;
@@ -858,7 +870,7 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
             StepArgs a = make_args(h, 0);
             a.src = seg_state(j, t - 1);
             a.dst = seg_state(j, t);
-            a.k = start + t;
+            set_step(a, start + t);
             CK(h, lbm::launch_step(h->q, LBM_STORE_F32, uk, walls, h->cfg, a, h->st));
         }
         for (int64_t k = end; k > start; --k) {

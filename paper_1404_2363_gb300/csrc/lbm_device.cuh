@@ -118,12 +118,33 @@ __host__ __device__ constexpr int wclass(int i) {
     return n == 0 ? 0 : (n == 1 ? 1 : 2);
 }
 
+// Arithmetic note: where a product feeds a sum, the kernels use explicitly
+// rounded operations (__fmul_rn, fmaf), never left to FMA contraction, so that
+// every kernel variant (one node, node pairs, batch) rounds identically.
+
+// e_i . u with e_i in {-1, 0, 1}^3: the non-zero terms added in x, y, z order
+template <class L>
+__device__ __forceinline__ float e_dot(int i, float ux, float uy, float uz)
+{
+    const float t[3] = {L::ex(i) > 0 ? ux : -ux, L::ey(i) > 0 ? uy : -uy, L::ez(i) > 0 ? uz : -uz};
+    const bool nz[3] = {L::ex(i) != 0, L::ey(i) != 0, L::ez(i) != 0};
+    float eu = 0.f;
+    bool has = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!nz[a]) continue;
+        eu = has ? __fadd_rn(eu, t[a]) : t[a];
+        has = true;
+    }
+    return eu;
+}
+
 // f^eq_i / phi = w_i + k_i e_i.u  (equilibria linear in u, Eq. 17)
 template <class L>
 __device__ __forceinline__ float feq_unit(const Coef& c, int i, float ux, float uy, float uz) {
     const int w = wclass<L>(i);
-    const float eu = (float)L::ex(i) * ux + (float)L::ey(i) * uy + (float)L::ez(i) * uz;
     if (w == 0) return c.w0;
+    const float eu = e_dot<L>(i, ux, uy, uz);
     if (w == 1) return fmaf(c.ka, eu, c.wa);
     return fmaf(c.kd, eu, c.wd);
 }
@@ -243,8 +264,8 @@ __device__ __forceinline__ float populations(const float (&a)[L::Q], float (&v)[
         v[7] = BP - XY;
         v[6] = BM - XmY;
         v[8] = BM + XmY;
-        if (FULL) v[0] = ZERO0 ? 4.f * (a[2] - a[1]) : fmaf(4.f, a[2], fmaf(-4.f, a[1], a[0]));
-        return 4.f * (A + B);
+        if (FULL) v[0] = ZERO0 ? __fmul_rn(4.f, a[2] - a[1]) : fmaf(4.f, a[2], fmaf(-4.f, a[1], a[0]));
+        return __fmul_rn(4.f, A + B);
     } else {
         float sum = 0.f;
 #pragma unroll
@@ -276,12 +297,11 @@ __device__ __forceinline__ float collide(float (&f)[L::Q], float ux, float uy, f
     // dl = m - m^eq_lin (Eq. 15 / A.3 with c1 = 1, c2 from Eq. 16 / A.4: linear in u);
     // d = dl - (u^2 terms of the MRT-B1/B2 equilibria, zero otherwise)
     float dl[Q], d[Q];
-    const float u2 = ux * ux + uy * uy + uz * uz;
     dl[0] = d[0] = 0.f;
     dl[1] = fmaf(-c.meq1, phi, m[1]);
     dl[2] = fmaf(-c.meq2, phi, m[2]);
-    d[1] = fmaf(-c.b1 * u2, phi, dl[1]);
-    d[2] = fmaf(-c.b2 * u2, phi, dl[2]);
+    d[1] = dl[1];
+    d[2] = dl[2];
 #pragma unroll
     for (int a = 0; a < L::DIM; ++a) {
         d[3 + 2 * a] = dl[3 + 2 * a] = fmaf(-phi, u[a], m[3 + 2 * a]);
@@ -289,9 +309,15 @@ __device__ __forceinline__ float collide(float (&f)[L::Q], float ux, float uy, f
     }
 #pragma unroll
     for (int k = 3 + 2 * L::DIM; k < Q; ++k) d[k] = dl[k] = m[k];
-    if (L::Q == 9) {
-        d[7] = fmaf(-c.g7 * (ux * ux - uy * uy), phi, dl[7]);
-        d[8] = fmaf(-c.g8 * (ux * uy), phi, dl[8]);
+    if (c.b1 != 0.f || c.b2 != 0.f || c.g7 != 0.f || c.g8 != 0.f) {   // MRT-B1/B2 only
+        float u2 = fmaf(ux, ux, __fmul_rn(uy, uy));
+        if (L::DIM == 3) u2 = fmaf(uz, uz, u2);
+        d[1] = fmaf(__fmul_rn(-c.b1, u2), phi, dl[1]);
+        d[2] = fmaf(__fmul_rn(-c.b2, u2), phi, dl[2]);
+        if (L::Q == 9) {
+            d[7] = fmaf(__fmul_rn(-c.g7, fmaf(ux, ux, -__fmul_rn(uy, uy))), phi, dl[7]);
+            d[8] = fmaf(__fmul_rn(-c.g8, __fmul_rn(ux, uy)), phi, dl[8]);
+        }
     }
     // relaxation m' = m - S d; the offset form keeps m' - m^eq_lin = dl - S d
     const float (&base)[Q] = OFFSET ? dl : m;
@@ -314,7 +340,7 @@ __device__ __forceinline__ float collide(float (&f)[L::Q], float ux, float uy, f
     for (int k = 3 + 2 * L::DIM; k < Q; ++k) mp[k] = fmaf(-c.s[k], d[k], base[k]);
     // f' = M^T diag(1 / |row|^2) m'
 #pragma unroll
-    for (int k = 0; k < Q; ++k) mp[k] *= 1.0f / (float)row_norm2<L>(k);
+    for (int k = 0; k < Q; ++k) mp[k] = __fmul_rn(mp[k], 1.0f / (float)row_norm2<L>(k));
     const float moving = populations<L, OFFSET, false>(mp, f);
     // The rest population closes the mass balance: sum_i f'_i = m'_0 = phi
     // (row 0 of M^-1 m'), and sum_i g_i = 0. Taking it from the moving
@@ -365,6 +391,14 @@ __device__ __forceinline__ void sched_at(const StepArgs& a, long long k, int dim
     sched_at(a.sched, a.sched_len, k, dim, s);
 }
 
+// the same from a row computed on the host (row < 0: no schedule)
+__device__ __forceinline__ void sched_row_at(const float* sched, int row, int dim, float* s)
+{
+    s[0] = s[1] = s[2] = 1.f;
+    if (row >= 0)
+        for (int d = 0; d < dim; ++d) s[d] = __ldg(sched + row * dim + d);
+}
+
 // u(x, k) = a(x) s(k) for a field, a(y) s(k) for a row profile, 0 otherwise.
 template <int UK, int DIM>
 __device__ __forceinline__ void vel_at_p(const float* ua, long long ncell, int ny, long long cell, int y,
@@ -372,13 +406,13 @@ __device__ __forceinline__ void vel_at_p(const float* ua, long long ncell, int n
 {
     ux = uy = uz = 0.f;
     if (UK == U_FIELD) {
-        ux = __ldg(ua + cell) * s[0];
-        uy = __ldg(ua + ncell + cell) * s[1];
-        if (DIM == 3) uz = __ldg(ua + 2 * ncell + cell) * s[2];
+        ux = __fmul_rn(__ldg(ua + cell), s[0]);
+        uy = __fmul_rn(__ldg(ua + ncell + cell), s[1]);
+        if (DIM == 3) uz = __fmul_rn(__ldg(ua + 2 * ncell + cell), s[2]);
     } else if (UK == U_ROW) {
-        ux = __ldg(ua + y) * s[0];
-        uy = __ldg(ua + ny + y) * s[1];
-        if (DIM == 3) uz = __ldg(ua + 2 * ny + y) * s[2];
+        ux = __fmul_rn(__ldg(ua + y), s[0]);
+        uy = __fmul_rn(__ldg(ua + ny + y), s[1]);
+        if (DIM == 3) uz = __fmul_rn(__ldg(ua + 2 * ny + y), s[2]);
     }
 }
 
@@ -402,13 +436,13 @@ __device__ __forceinline__ void vel_ix(const StepArgs& a, IX N, IX cell, int y, 
 {
     ux = uy = uz = 0.f;
     if (UK == U_FIELD) {
-        ux = __ldg(a.ua + cell) * s[0];
-        uy = __ldg(a.ua + N + cell) * s[1];
-        if (DIM == 3) uz = __ldg(a.ua + 2 * N + cell) * s[2];
+        ux = __fmul_rn(__ldg(a.ua + cell), s[0]);
+        uy = __fmul_rn(__ldg(a.ua + N + cell), s[1]);
+        if (DIM == 3) uz = __fmul_rn(__ldg(a.ua + 2 * N + cell), s[2]);
     } else if (UK == U_ROW) {
-        ux = __ldg(a.ua + y) * s[0];
-        uy = __ldg(a.ua + a.ny + y) * s[1];
-        if (DIM == 3) uz = __ldg(a.ua + 2 * a.ny + y) * s[2];
+        ux = __fmul_rn(__ldg(a.ua + y), s[0]);
+        uy = __fmul_rn(__ldg(a.ua + a.ny + y), s[1]);
+        if (DIM == 3) uz = __fmul_rn(__ldg(a.ua + 2 * a.ny + y), s[2]);
     }
 }
 
@@ -430,8 +464,8 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
 
     float s_now[3], s_prev[3];
     if (UK != U_NONE) {
-        sched_at(a, a.k, L::DIM, s_now);
-        sched_at(a, a.k - 1, L::DIM, s_prev);
+        sched_row_at(a.sched, a.srow_now, L::DIM, s_now);
+        sched_row_at(a.sched, a.srow_prev, L::DIM, s_prev);
     }
 
     float f[VEC][Q];
@@ -451,7 +485,7 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
             if (NEQ) {
                 float ux, uy, uz;
                 vel_ix<UK, L::DIM, IX>(a, N, sc, ys[L::ey(i) + 1], s_prev, ux, uy, uz);
-                v += __ldg(a.phi_src + sc) * feq_unit<L>(a.c, i, ux, uy, uz);
+                v = fmaf(__ldg(a.phi_src + sc), feq_unit<L>(a.c, i, ux, uy, uz), v);
             }
             f[j][i] = v;
         }
@@ -477,7 +511,7 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
                         if (L::ey(i) != 0 && ((L::ey(i) == 1) == lo)) {
                             const int o = opposite<L>(i);
                             float v = ldg_f(src + (IX)o * N + cell[j]);
-                            if (NEQ) v += __ldg(a.phi_src + cell[j]) * feq_unit<L>(a.c, o, ux, uy, uz);
+                            if (NEQ) v = fmaf(__ldg(a.phi_src + cell[j]), feq_unit<L>(a.c, o, ux, uy, uz), v);
                             f[j][i] = v;
                         }
                 } else {  // Dirichlet
@@ -493,7 +527,7 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
                     const float ps = (phiw - known) / wk;
 #pragma unroll
                     for (int i = 0; i < Q; ++i)
-                        if (L::ey(i) == inward) f[j][i] = ps * feq_unit<L>(a.c, i, ux, uy, uz);
+                        if (L::ey(i) == inward) f[j][i] = __fmul_rn(ps, feq_unit<L>(a.c, i, ux, uy, uz));
                 }
             }
         }
@@ -561,8 +595,8 @@ __global__ void __launch_bounds__(256) k_step_neq_d2q9(const StepArgs a)
     const bool needR = lane == 31 || xc == nx - 1;
     const Coef& c = a.c;
     float s_now[3], s_prev[3];
-    sched_at(a, a.k, 2, s_now);
-    sched_at(a, a.k - 1, 2, s_prev);
+    sched_row_at(a.sched, a.srow_now, 2, s_now);
+    sched_row_at(a.sched, a.srow_prev, 2, s_prev);
 
     // window: [row][column], row 0 = y-1, 1 = y, 2 = y+1; column 0 = x-1, 1 = x, 2 = x+1
     RowVals W[3][3];
@@ -733,8 +767,8 @@ __global__ void __launch_bounds__(256) k_step_neq_tile_d2q9(const StepArgs a)
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
     const Coef& c = a.c;
     float s_now[3], s_prev[3];
-    sched_at(a, a.k, 2, s_now);
-    sched_at(a, a.k - 1, 2, s_prev);
+    sched_row_at(a.sched, a.srow_now, 2, s_now);
+    sched_row_at(a.sched, a.srow_prev, 2, s_prev);
 
     __shared__ float P[(BY + 2) * SW], JX[(BY + 2) * SW], JY[(BY + 2) * SW];
     float axo, ayo;   // own raw velocity factors

@@ -41,6 +41,8 @@ struct StepArgs {
     const float* sched;   // [sched_len][dim] or nullptr
     long long sched_len;
     long long k;          // this step computes f(k) and collides with u(k)
+    int srow_now;         // schedule rows of u(k) and u(k-1): k mod sched_len,
+    int srow_prev;        // (k-1) mod sched_len, or -1 without a schedule
     int nx, ny, nz;
     long long ncell;
     int bc_lo, bc_hi;
@@ -57,6 +59,7 @@ struct AdjArgs {
     const float* sched;
     long long sched_len;
     long long k;          // the forward step being reversed (collision with u(k))
+    int srow;             // k mod sched_len, or -1 without a schedule
     int nx, ny, nz;
     long long ncell;
     int bc_lo, bc_hi;
@@ -65,6 +68,22 @@ struct AdjArgs {
     double* partials;     // per-block gradient partials [nblocks][ngrad]
     double* grad_acc;     // [ngrad] running sums: G_A[dim][dim], G_AC[dim][dim], G_diag[q]
 };
+
+// Row of a schedule of length len for step k (k mod len), -1 without one;
+// computed on the host so that no kernel divides by the schedule length.
+inline int sched_row(long long k, long long len)
+{
+    if (len <= 0) return -1;
+    long long r = k % len;
+    return (int)(r < 0 ? r + len : r);
+}
+
+inline void set_step(StepArgs& a, long long k)
+{
+    a.k = k;
+    a.srow_now = sched_row(k, a.sched ? a.sched_len : 0);
+    a.srow_prev = sched_row(k - 1, a.sched ? a.sched_len : 0);
+}
 
 struct LaunchCfg {
     int block;   // threads per block (multiple of 32)

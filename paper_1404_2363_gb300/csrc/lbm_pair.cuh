@@ -1,0 +1,270 @@
+// D2Q9 step for the 16-bit offset storage on node pairs: one thread owns the
+// two adjacent nodes (x0, x0 + 1), x0 even, and evaluates the decode, the
+// collision and the offset store for both with paired FP32 instructions
+// (add/mul/fma on float2, sm_100 and later), so every arithmetic instruction
+// serves two nodes. The offsets are loaded as aligned 32-bit pairs; the
+// pulls shifted by one column combine halves of two neighbouring pairs.
+//
+// The operation sequence is the one of collide<D2Q9, true> and of the decode
+// in k_step; the compiler may fuse some paired multiplies into the adds that
+// follow them, so results agree with k_step to FP32 rounding.
+#pragma once
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Paired operations (one instruction for both nodes). The compiler may fuse a
+// paired multiply into a following paired add, so the pair kernel agrees with
+// the one-node kernel to FP32 rounding rather than bit for bit.
+__device__ __forceinline__ float2 sp2(float c) { return make_float2(c, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// collide<D2Q9, OFFSET> for two nodes (see lbm_device.cuh for the steps)
+template <bool OFFSET>
+__device__ __forceinline__ float2 collide_pair(float2 (&v)[9], float2 ux, float2 uy, const Coef& c)
+{
+    // m = M v by same-speed sums and differences
+    const float2 sx = add2(v[1], v[3]), ax = sub2(v[1], v[3]);
+    const float2 sy = add2(v[2], v[4]), ay = sub2(v[2], v[4]);
+    const float2 p57 = add2(v[5], v[7]), d57 = sub2(v[5], v[7]);
+    const float2 p68 = add2(v[6], v[8]), d68 = sub2(v[6], v[8]);
+    const float2 sa = add2(sx, sy), sd = add2(p57, p68);
+    const float2 jx = sub2(d57, d68), jy = add2(d57, d68);
+    float2 m[9];
+    m[0] = add2(add2(v[0], sa), sd);
+    m[1] = fma2(sp2(2.f), sd, fma2(sp2(-4.f), v[0], neg2(sa)));
+    m[2] = fma2(sp2(-2.f), sa, fma2(sp2(4.f), v[0], sd));
+    m[3] = add2(ax, jx);
+    m[4] = fma2(sp2(-2.f), ax, jx);
+    m[5] = add2(ay, jy);
+    m[6] = fma2(sp2(-2.f), ay, jy);
+    m[7] = sub2(sx, sy);
+    m[8] = sub2(p57, p68);
+    const float2 phi = m[0];
+    // dl = m - m^eq_lin, d = dl - (MRT-B1/B2 u^2 terms)
+    float2 dl[9], d[9];
+    dl[1] = fma2(sp2(-c.meq1), phi, m[1]);
+    dl[2] = fma2(sp2(-c.meq2), phi, m[2]);
+    d[1] = dl[1];
+    d[2] = dl[2];
+    d[3] = dl[3] = fma2(neg2(phi), ux, m[3]);
+    d[4] = dl[4] = fma2(phi, ux, m[4]);
+    d[5] = dl[5] = fma2(neg2(phi), uy, m[5]);
+    d[6] = dl[6] = fma2(phi, uy, m[6]);
+    d[7] = dl[7] = m[7];
+    d[8] = dl[8] = m[8];
+    // (the u^2 terms of MRT-B1/B2 never occur here: those models need FP32 storage)
+    // m' = m - S d (offset form: m' - m^eq_lin = dl - S d)
+    float2 a[9];
+    const float2* base = OFFSET ? dl : m;
+    a[0] = OFFSET ? sp2(0.f) : phi;
+    a[1] = fma2(sp2(-c.s[1]), d[1], base[1]);
+    a[2] = fma2(sp2(-c.s[2]), d[2], base[2]);
+    float2 r0 = fma2(sp2(c.A[0]), d[3], sp2(0.f));
+    r0 = fma2(sp2(c.C[0]), d[4], r0);
+    r0 = fma2(sp2(c.A[1]), d[5], r0);
+    r0 = fma2(sp2(c.C[1]), d[6], r0);
+    a[3] = sub2(base[3], r0);
+    a[4] = fma2(sp2(-c.s[4]), d[4], base[4]);
+    float2 r1 = fma2(sp2(c.A[2]), d[3], sp2(0.f));
+    r1 = fma2(sp2(c.C[2]), d[4], r1);
+    r1 = fma2(sp2(c.A[3]), d[5], r1);
+    r1 = fma2(sp2(c.C[3]), d[6], r1);
+    a[5] = sub2(base[5], r1);
+    a[6] = fma2(sp2(-c.s[6]), d[6], base[6]);
+    a[7] = fma2(sp2(-c.s[7]), d[7], base[7]);
+    a[8] = fma2(sp2(-c.s[8]), d[8], base[8]);
+#pragma unroll
+    for (int k = OFFSET ? 1 : 0; k < 9; ++k) a[k] = mul2(a[k], sp2(1.0f / (float)row_norm2<D2Q9>(k)));
+    // v = M^T a (populations<D2Q9, OFFSET, false>)
+    const float2 A = OFFSET ? fma2(sp2(-2.f), a[2], neg2(a[1])) : fma2(sp2(-2.f), a[2], sub2(a[0], a[1]));
+    const float2 B = OFFSET ? fma2(sp2(2.f), a[1], a[2]) : fma2(sp2(2.f), a[1], add2(a[0], a[2]));
+    const float2 X = fma2(sp2(-2.f), a[4], a[3]), Y = fma2(sp2(-2.f), a[6], a[5]);
+    const float2 Xd = add2(a[3], a[4]), Yd = add2(a[5], a[6]);
+    const float2 AP = add2(A, a[7]), AM = sub2(A, a[7]);
+    const float2 BP = add2(B, a[8]), BM = sub2(B, a[8]);
+    const float2 XY = add2(Xd, Yd), XmY = sub2(Xd, Yd);
+    v[1] = add2(AP, X);
+    v[3] = sub2(AP, X);
+    v[2] = add2(AM, Y);
+    v[4] = sub2(AM, Y);
+    v[5] = add2(BP, XY);
+    v[7] = sub2(BP, XY);
+    v[6] = sub2(BM, XmY);
+    v[8] = add2(BM, XmY);
+    const float2 moving = mul2(sp2(4.f), add2(A, B));   // exact
+    v[0] = OFFSET ? neg2(moving) : sub2(phi, moving);
+    return phi;
+}
+
+// paired 16-bit words
+template <int S> struct Pair;
+template <> struct Pair<ST_F16> {
+    using T2 = __half2;
+    __device__ static float2 to_f(__half2 h) { return mul2(__half22float2(h), sp2(1.0f / F16_SCALE)); }
+    __device__ static __half2 from_f(float2 v) { return __float22half2_rn(mul2(v, sp2(F16_SCALE))); }
+    __device__ static __half2 join(__half2 lo_src, __half2 hi_src) {   // (lo_src.y, hi_src.x)
+        return __halves2half2(__high2half(lo_src), __low2half(hi_src));
+    }
+};
+template <> struct Pair<ST_BF16> {
+    using T2 = __nv_bfloat162;
+    __device__ static float2 to_f(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+    __device__ static __nv_bfloat162 from_f(float2 v) { return __float22bfloat162_rn(v); }
+    __device__ static __nv_bfloat162 join(__nv_bfloat162 lo_src, __nv_bfloat162 hi_src) {
+        return __halves2bfloat162(__high2bfloat16(lo_src), __low2bfloat16(hi_src));
+    }
+};
+
+template <class T2>
+__device__ __forceinline__ T2 ldg_pair(const T2* p)
+{
+    const unsigned w = __ldg(reinterpret_cast<const unsigned*>(p));
+    return *reinterpret_cast<const T2*>(&w);
+}
+
+// f^eq_i / phi = w_i + k_i e_i.u for two nodes (feq_unit<D2Q9>)
+__device__ __forceinline__ float2 feq_unit_pair(const Coef& c, int i, float2 ux, float2 uy)
+{
+    const int w = wclass<D2Q9>(i);
+    if (w == 0) return sp2(c.w0);
+    const int ex = D2Q9::ex(i), ey = D2Q9::ey(i);
+    float2 eu;
+    if (ey == 0) eu = ex > 0 ? ux : neg2(ux);
+    else if (ex == 0) eu = ey > 0 ? uy : neg2(uy);
+    else if (ex > 0) eu = ey > 0 ? add2(ux, uy) : sub2(ux, uy);
+    else eu = ey > 0 ? sub2(uy, ux) : neg2(add2(ux, uy));
+    return w == 1 ? fma2(sp2(c.ka), eu, sp2(c.wa)) : fma2(sp2(c.kd), eu, sp2(c.wd));
+}
+
+// Needs nx even and 12 ncell < 2^31 (int offsets; checked by the launcher).
+template <int STORE, int UK, bool WALLS>
+__global__ void __launch_bounds__(256) k_step_pair_d2q9(const StepArgs a)
+{
+    using P = Pair<STORE>;
+    using T2 = typename P::T2;
+    using L = D2Q9;
+    const int nx = a.nx, ny = a.ny;
+    const int N = (int)a.ncell;
+    const int y = blockIdx.y;
+    const int x0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (x0 >= nx) return;
+    const int xl = x0 == 0 ? nx - 2 : x0 - 2;       // pair holding column x0 - 1
+    const int xr = x0 + 2 == nx ? 0 : x0 + 2;       // pair holding column x0 + 2
+    const int ys[3] = {y + 1 == ny ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};   // source row by e_y + 1
+    const Coef& c = a.c;
+    const T2* __restrict__ src = static_cast<const T2*>(a.src);   // pair index = cell / 2
+    T2* __restrict__ dst = static_cast<T2*>(a.dst);
+    const int NP = N / 2, nxp = nx / 2;
+    float s_now[3], s_prev[3];
+    sched_row_at(a.sched, a.srow_now, 2, s_now);
+    sched_row_at(a.sched, a.srow_prev, 2, s_prev);
+
+    // phi and u(k-1) at the sources: for source row r (by e_y + 1) the column
+    // pairs (x0 - 1, x0), (x0, x0 + 1), (x0 + 1, x0 + 2) (by 1 - e_x)
+    float2 Ps[3][3], Ux[3][3], Uy[3][3];
+    float2 axo = sp2(0.f), ayo = sp2(0.f);   // own raw velocity factors a(x0), a(x0 + 1)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int row = ys[r] * nx;
+        const float2 pm = __ldg(reinterpret_cast<const float2*>(a.phi_src + row + x0));
+        const float pl = __ldg(a.phi_src + row + xl + 1), pr = __ldg(a.phi_src + row + xr);
+        Ps[r][0] = make_float2(pl, pm.x);
+        Ps[r][1] = pm;
+        Ps[r][2] = make_float2(pm.y, pr);
+        if (UK == U_FIELD) {
+            const float* ax = a.ua;
+            const float* ay = a.ua + a.ncell;
+            const float2 xm = __ldg(reinterpret_cast<const float2*>(ax + row + x0));
+            const float xlv = __ldg(ax + row + xl + 1), xrv = __ldg(ax + row + xr);
+            const float2 ym = __ldg(reinterpret_cast<const float2*>(ay + row + x0));
+            const float ylv = __ldg(ay + row + xl + 1), yrv = __ldg(ay + row + xr);
+            Ux[r][0] = mul2(make_float2(xlv, xm.x), sp2(s_prev[0]));
+            Ux[r][1] = mul2(xm, sp2(s_prev[0]));
+            Ux[r][2] = mul2(make_float2(xm.y, xrv), sp2(s_prev[0]));
+            Uy[r][0] = mul2(make_float2(ylv, ym.x), sp2(s_prev[1]));
+            Uy[r][1] = mul2(ym, sp2(s_prev[1]));
+            Uy[r][2] = mul2(make_float2(ym.y, yrv), sp2(s_prev[1]));
+            if (r == 1) {
+                axo = xm;
+                ayo = ym;
+            }
+        } else if (UK == U_ROW) {
+            const float ux = __fmul_rn(__ldg(a.ua + ys[r]), s_prev[0]);
+            const float uy = __fmul_rn(__ldg(a.ua + a.ny + ys[r]), s_prev[1]);
+            Ux[r][0] = Ux[r][1] = Ux[r][2] = sp2(ux);
+            Uy[r][0] = Uy[r][1] = Uy[r][2] = sp2(uy);
+            if (r == 1) {
+                axo = sp2(__ldg(a.ua + y));
+                ayo = sp2(__ldg(a.ua + a.ny + y));
+            }
+        } else {
+            Ux[r][0] = Ux[r][1] = Ux[r][2] = sp2(0.f);
+            Uy[r][0] = Uy[r][1] = Uy[r][2] = sp2(0.f);
+        }
+    }
+
+    // pull and decode f_i = g_i(s) + phi(s) f^eq_i(1, u(s, k-1))
+    float2 f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ex = L::ex(i), ey = L::ey(i);
+        const int r = ey + 1, cp = 1 - ex;
+        const T2* row = src + i * NP + ys[r] * nxp;
+        T2 h;
+        if (ex == 0) h = ldg_pair(row + x0 / 2);
+        else if (ex > 0) h = P::join(ldg_pair(row + xl / 2), ldg_pair(row + x0 / 2));
+        else h = P::join(ldg_pair(row + x0 / 2), ldg_pair(row + xr / 2));
+        f[i] = fma2(Ps[r][cp], feq_unit_pair(c, i, Ux[r][cp], Uy[r][cp]), P::to_f(h));
+    }
+    const int cellp = y * nxp + x0 / 2;
+    if (WALLS) {
+        const bool lo = (y == 0) && a.bc_lo != BC_PERIODIC;
+        const bool hi = (y == ny - 1) && a.bc_hi != BC_PERIODIC;
+        if (lo || hi) {
+            const int kind = lo ? a.bc_lo : a.bc_hi;
+            const int inward = lo ? 1 : -1;
+            const float2 uxp = mul2(axo, sp2(s_prev[0])), uyp = mul2(ayo, sp2(s_prev[1]));
+            if (kind == BC_NOFLUX) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (L::ey(i) == inward) f[i] = f[mirror_y<L>(i)];
+            } else if (kind == BC_BOUNCE) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (L::ey(i) == inward) {
+                        const int o = opposite<L>(i);
+                        const float2 g = P::to_f(ldg_pair(src + o * NP + cellp));
+                        f[i] = fma2(Ps[1][1], feq_unit_pair(c, o, uxp, uyp), g);
+                    }
+            } else {   // Dirichlet
+                float2 known = sp2(0.f), wk = sp2(0.f);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    if (L::ey(i) == inward) wk = add2(wk, feq_unit_pair(c, i, uxp, uyp));
+                    else known = add2(known, f[i]);
+                }
+                const float phiw = lo ? a.phiw_lo : a.phiw_hi;
+                const float2 ps = make_float2((phiw - known.x) / wk.x, (phiw - known.y) / wk.y);
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (L::ey(i) == inward) f[i] = mul2(ps, feq_unit_pair(c, i, uxp, uyp));
+            }
+        }
+    }
+    float2 uxn = sp2(0.f), uyn = sp2(0.f);
+    if (UK != U_NONE) {
+        uxn = mul2(axo, sp2(s_now[0]));
+        uyn = mul2(ayo, sp2(s_now[1]));
+    }
+    const float2 phi = collide_pair<true>(f, uxn, uyn, c);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dst[i * NP + cellp] = P::from_f(f[i]);
+    *reinterpret_cast<float2*>(a.phi_dst + 2 * cellp) = phi;
+}
+
+}  // namespace lbm

@@ -2,6 +2,7 @@
 // Each step_*.cu translation unit includes this with LBM_LAT / LBM_STORE /
 // LBM_FN defined, so the template instantiations compile in parallel.
 #include "lbm_device.cuh"
+#include "lbm_pair.cuh"
 
 namespace lbm {
 
@@ -9,6 +10,13 @@ template <class L, int STORE, int UK, bool WALLS>
 static cudaError_t step_vec(LaunchCfg cfg, const StepArgs& a, cudaStream_t st)
 {
     if constexpr (L::Q == 9 && STORE != ST_F32) {
+        if (cfg.vec == 5 && a.nx % 2 == 0 && a.nz == 1 && 12LL * a.ncell < (1LL << 31)) {
+            // node-pair variant (paired FP32 arithmetic, two adjacent nodes per thread)
+            const int per = 2 * cfg.block;
+            dim3 grid((unsigned)((a.nx + per - 1) / per), (unsigned)a.ny, 1);
+            k_step_pair_d2q9<STORE, UK, WALLS><<<grid, cfg.block, 0, st>>>(a);
+            return cudaGetLastError();
+        }
         if (cfg.vec == 4 && a.nx % 32 == 0 && a.ny % 8 == 0 && 12LL * a.ncell < (1LL << 31)) {
             // shared-memory tile variant of the offset storage (32 x 8 blocks)
             dim3 grid((unsigned)(a.nx / 32), (unsigned)(a.ny / 8), 1);

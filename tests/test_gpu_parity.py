@@ -131,12 +131,35 @@ def test_tile_offset_kernel(O, storage, bc, ukind):
     assert rel_l2(got, want) <= TOL[storage]
 
 
-def _run_vec3(case, phi0, a, sched, vec=3):
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("bc,ukind", [(("periodic", "periodic"), "field"), (("noflux", "noflux"), "row"),
+                                      (("bounceback", "bounceback"), "field"),
+                                      (("dirichlet", "dirichlet"), "field"), (("periodic", "periodic"), "none")])
+def test_pair_offset_kernel(O, storage, bc, ukind):
+    """The node-pair kernel of the 16-bit forms (launch vec = 5, paired FP32
+    arithmetic) against the oracle on a 302 x 37 grid (151 pairs per row: ragged
+    64-thread blocks), and against the one-node kernel: the same operations, up to
+    the compiler's fusing of paired multiply-adds, so the fields agree to the
+    16-bit rounding of a few offsets."""
+    case = Case(storage=storage, bc=bc, ukind=ukind, sched=ukind != "none", nx=302, ny=37,
+                phi_w=(1.0, 0.25) if bc[0] == "dirichlet" else (0.0, 0.0))
+    phi0, a, sched = case.inputs()
+    got, _ = _run_vec3(case, phi0, a, sched, vec=5, block=64)
+    want = run_oracle(O, case, phi0, a, sched)
+    assert rel_l2(got, want) <= TOL[storage]
+    one, _ = _run_vec3(case, phi0, a, sched, vec=1, block=64)
+    assert rel_l2(got, one) <= TOL[storage] / 4
+    if ukind != "field":   # no products with a varying velocity: nothing to fuse differently
+        assert np.array_equal(got, one)
+
+
+def _run_vec3(case, phi0, a, sched, vec=3, block=256):
     import torch
     from paper_1404_2363_gb300.solver import Solver
 
-    s = Solver(nx=case.nx, ny=case.ny, storage=case.storage, bc=case.bc, phi_w=case.phi_w)
-    s.set_launch(256, vec)
+    s = Solver(nx=case.nx, ny=case.ny, storage=case.storage, bc=case.bc, phi_w=case.phi_w,
+               model=case.model)
+    s.set_launch(block, vec)
     s.set_D(case.D)
     if a is not None:
         s.set_velocity(torch.from_numpy(a).cuda(), None if sched is None else torch.from_numpy(sched).cuda(),
@@ -163,5 +186,8 @@ def test_autotune_keeps_results(tmp_path, monkeypatch):
     assert s.t == 0
     s.step(case.steps)
     got = s.get_phi().cpu().numpy().astype(np.float64)
-    assert rel_l2(got, ref) < 1e-6, shape
+    assert rel_l2(got, ref) < TOL["bf16"] / 4, shape
+    # the state was restored: the tuned shape from scratch gives the same field
+    again, _ = _run_vec3(case, phi0, a, sched, vec=shape[1], block=shape[0])
+    assert np.array_equal(got, again), shape
     assert (tmp_path / "tune.txt").read_text().strip().endswith(f"{shape[0]} {shape[1]}")
