@@ -186,6 +186,7 @@ static void refresh_coef(lbm_cde_t h)
         c.wd = (float)((2.0 * a1 + a2 + 16.0) / 144.0);
         c.ka = (float)(48.0 / 144.0);
         c.kd = (float)(12.0 / 144.0);
+        lbm::fold_offset_coef(c);
     } else {
         c.meq1 = (float)(5.0 * a1 / 6.0);
         c.meq2 = (float)(a2 / 24.0);

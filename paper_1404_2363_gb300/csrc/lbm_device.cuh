@@ -293,6 +293,25 @@ __device__ __forceinline__ float collide(float (&f)[L::Q], float ux, float uy, f
     float m[Q];
     moments<L>(f, m);
     const float phi = m[0];
+    if constexpr (OFFSET && L::Q == 9) {
+        // offsets of the 16-bit forms (linear equilibria only): with dl = m - m^eq,
+        // a = diag(1/|M_k|^2) (I - S) dl, the rates and scales folded in c.ro, c.fr
+        const float dl1 = fmaf(-c.meq1, phi, m[1]), dl2 = fmaf(-c.meq2, phi, m[2]);
+        const float dl3 = fmaf(-phi, ux, m[3]), dl4 = fmaf(phi, ux, m[4]);
+        const float dl5 = fmaf(-phi, uy, m[5]), dl6 = fmaf(phi, uy, m[6]);
+        float a[9];
+        a[0] = 0.f;
+        a[1] = __fmul_rn(dl1, c.ro[1]);
+        a[2] = __fmul_rn(dl2, c.ro[2]);
+        a[4] = __fmul_rn(dl4, c.ro[4]);
+        a[6] = __fmul_rn(dl6, c.ro[6]);
+        a[7] = __fmul_rn(m[7], c.ro[7]);
+        a[8] = __fmul_rn(m[8], c.ro[8]);
+        a[3] = fmaf(c.fr[0], dl3, fmaf(c.fr[1], dl4, fmaf(c.fr[2], dl5, __fmul_rn(c.fr[3], dl6))));
+        a[5] = fmaf(c.fr[4], dl3, fmaf(c.fr[5], dl4, fmaf(c.fr[6], dl5, __fmul_rn(c.fr[7], dl6))));
+        f[0] = -populations<L, true, false>(a, f);
+        return phi;
+    }
     const float u[3] = {ux, uy, uz};
     // dl = m - m^eq_lin (Eq. 15 / A.3 with c1 = 1, c2 from Eq. 16 / A.4: linear in u);
     // d = dl - (u^2 terms of the MRT-B1/B2 equilibria, zero otherwise)

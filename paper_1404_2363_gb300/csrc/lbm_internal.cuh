@@ -30,7 +30,27 @@ struct Coef {
     // u^2 terms of the MRT-B1/B2 equilibria (Eq. 38-39), zero for MRT-A/B3:
     //   m1 += b1 |u|^2 phi, m2 += b2 |u|^2 phi, m7 = g7 (ux^2 - uy^2) phi, m8 = g8 ux uy phi
     float b1, b2, g7, g8;
+    // D2Q9 offset form (linear equilibria): the relaxation and the 1/|M_k|^2
+    // scaling folded together, a_k = (m' - m^eq)_k / |M_k|^2 from dl = m - m^eq:
+    //   ro[k] = (1 - s_k) / |M_k|^2                      (k = 1, 2, 4, 6, 7, 8)
+    //   fr[4 r + j]: flux row 3 + 2 r on dl_3, dl_4, dl_5, dl_6
+    //               ((delta_r0 - A_r0) / 6, -C_r0 / 6, (delta_r1 - A_r1) / 6, -C_r1 / 6)
+    float ro[9];
+    float fr[8];
 };
+
+// Fills ro and fr from s, A and C (D2Q9; host side).
+inline void fold_offset_coef(Coef& c)
+{
+    const double n2[9] = {9, 36, 36, 6, 12, 6, 12, 4, 4};
+    for (int k = 0; k < 9; ++k) c.ro[k] = (float)((1.0 - (double)c.s[k]) / n2[k]);
+    for (int r = 0; r < 2; ++r) {
+        c.fr[4 * r + 0] = (float)(((r == 0 ? 1.0 : 0.0) - (double)c.A[2 * r + 0]) / 6.0);
+        c.fr[4 * r + 1] = (float)(-(double)c.C[2 * r + 0] / 6.0);
+        c.fr[4 * r + 2] = (float)(((r == 1 ? 1.0 : 0.0) - (double)c.A[2 * r + 1]) / 6.0);
+        c.fr[4 * r + 3] = (float)(-(double)c.C[2 * r + 1] / 6.0);
+    }
+}
 
 struct StepArgs {
     const void* src;      // state planes [q][ncell] (float or 16-bit)

@@ -23,8 +23,8 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// collide<D2Q9, OFFSET> for two nodes (see lbm_device.cuh for the steps)
-template <bool OFFSET>
+// collide<D2Q9, true> for two nodes: the offsets g = M^-1 (m' - m^eq) of the
+// 16-bit forms, whose equilibria are linear in u (see lbm_device.cuh)
 __device__ __forceinline__ float2 collide_pair(float2 (&v)[9], float2 ux, float2 uy, const Coef& c)
 {
     // m = M v by same-speed sums and differences
@@ -34,59 +34,28 @@ __device__ __forceinline__ float2 collide_pair(float2 (&v)[9], float2 ux, float2
     const float2 p68 = add2(v[6], v[8]), d68 = sub2(v[6], v[8]);
     const float2 sa = add2(sx, sy), sd = add2(p57, p68);
     const float2 jx = sub2(d57, d68), jy = add2(d57, d68);
-    float2 m[9];
-    m[0] = add2(add2(v[0], sa), sd);
-    m[1] = fma2(sp2(2.f), sd, fma2(sp2(-4.f), v[0], neg2(sa)));
-    m[2] = fma2(sp2(-2.f), sa, fma2(sp2(4.f), v[0], sd));
-    m[3] = add2(ax, jx);
-    m[4] = fma2(sp2(-2.f), ax, jx);
-    m[5] = add2(ay, jy);
-    m[6] = fma2(sp2(-2.f), ay, jy);
-    m[7] = sub2(sx, sy);
-    m[8] = sub2(p57, p68);
-    const float2 phi = m[0];
-    // dl = m - m^eq_lin, d = dl - (MRT-B1/B2 u^2 terms)
-    float2 dl[9], d[9];
-    dl[1] = fma2(sp2(-c.meq1), phi, m[1]);
-    dl[2] = fma2(sp2(-c.meq2), phi, m[2]);
-    d[1] = dl[1];
-    d[2] = dl[2];
-    d[3] = dl[3] = fma2(neg2(phi), ux, m[3]);
-    d[4] = dl[4] = fma2(phi, ux, m[4]);
-    d[5] = dl[5] = fma2(neg2(phi), uy, m[5]);
-    d[6] = dl[6] = fma2(phi, uy, m[6]);
-    d[7] = dl[7] = m[7];
-    d[8] = dl[8] = m[8];
-    // (the u^2 terms of MRT-B1/B2 never occur here: those models need FP32 storage)
-    // m' = m - S d (offset form: m' - m^eq_lin = dl - S d)
-    float2 a[9];
-    const float2* base = OFFSET ? dl : m;
-    a[0] = OFFSET ? sp2(0.f) : phi;
-    a[1] = fma2(sp2(-c.s[1]), d[1], base[1]);
-    a[2] = fma2(sp2(-c.s[2]), d[2], base[2]);
-    float2 r0 = fma2(sp2(c.A[0]), d[3], sp2(0.f));
-    r0 = fma2(sp2(c.C[0]), d[4], r0);
-    r0 = fma2(sp2(c.A[1]), d[5], r0);
-    r0 = fma2(sp2(c.C[1]), d[6], r0);
-    a[3] = sub2(base[3], r0);
-    a[4] = fma2(sp2(-c.s[4]), d[4], base[4]);
-    float2 r1 = fma2(sp2(c.A[2]), d[3], sp2(0.f));
-    r1 = fma2(sp2(c.C[2]), d[4], r1);
-    r1 = fma2(sp2(c.A[3]), d[5], r1);
-    r1 = fma2(sp2(c.C[3]), d[6], r1);
-    a[5] = sub2(base[5], r1);
-    a[6] = fma2(sp2(-c.s[6]), d[6], base[6]);
-    a[7] = fma2(sp2(-c.s[7]), d[7], base[7]);
-    a[8] = fma2(sp2(-c.s[8]), d[8], base[8]);
-#pragma unroll
-    for (int k = OFFSET ? 1 : 0; k < 9; ++k) a[k] = mul2(a[k], sp2(1.0f / (float)row_norm2<D2Q9>(k)));
-    // v = M^T a (populations<D2Q9, OFFSET, false>)
-    const float2 A = OFFSET ? fma2(sp2(-2.f), a[2], neg2(a[1])) : fma2(sp2(-2.f), a[2], sub2(a[0], a[1]));
-    const float2 B = OFFSET ? fma2(sp2(2.f), a[1], a[2]) : fma2(sp2(2.f), a[1], add2(a[0], a[2]));
-    const float2 X = fma2(sp2(-2.f), a[4], a[3]), Y = fma2(sp2(-2.f), a[6], a[5]);
-    const float2 Xd = add2(a[3], a[4]), Yd = add2(a[5], a[6]);
-    const float2 AP = add2(A, a[7]), AM = sub2(A, a[7]);
-    const float2 BP = add2(B, a[8]), BM = sub2(B, a[8]);
+    const float2 phi = add2(add2(v[0], sa), sd);
+    const float2 m1 = fma2(sp2(2.f), sd, fma2(sp2(-4.f), v[0], neg2(sa)));
+    const float2 m2 = fma2(sp2(-2.f), sa, fma2(sp2(4.f), v[0], sd));
+    const float2 m3 = add2(ax, jx), m4 = fma2(sp2(-2.f), ax, jx);
+    const float2 m5 = add2(ay, jy), m6 = fma2(sp2(-2.f), ay, jy);
+    const float2 m7 = sub2(sx, sy), m8 = sub2(p57, p68);
+    // dl = m - m^eq; a = diag(1/|M_k|^2) (I - S) dl with the folded c.ro, c.fr
+    const float2 dl1 = fma2(sp2(-c.meq1), phi, m1), dl2 = fma2(sp2(-c.meq2), phi, m2);
+    const float2 dl3 = fma2(neg2(phi), ux, m3), dl4 = fma2(phi, ux, m4);
+    const float2 dl5 = fma2(neg2(phi), uy, m5), dl6 = fma2(phi, uy, m6);
+    const float2 a1 = mul2(dl1, sp2(c.ro[1])), a2 = mul2(dl2, sp2(c.ro[2]));
+    const float2 a4 = mul2(dl4, sp2(c.ro[4])), a6 = mul2(dl6, sp2(c.ro[6]));
+    const float2 a7 = mul2(m7, sp2(c.ro[7])), a8 = mul2(m8, sp2(c.ro[8]));
+    const float2 a3 = fma2(sp2(c.fr[0]), dl3, fma2(sp2(c.fr[1]), dl4, fma2(sp2(c.fr[2]), dl5, mul2(sp2(c.fr[3]), dl6))));
+    const float2 a5 = fma2(sp2(c.fr[4]), dl3, fma2(sp2(c.fr[5]), dl4, fma2(sp2(c.fr[6]), dl5, mul2(sp2(c.fr[7]), dl6))));
+    // v = M^T a (populations<D2Q9, true, false>)
+    const float2 A = fma2(sp2(-2.f), a2, neg2(a1));
+    const float2 B = fma2(sp2(2.f), a1, a2);
+    const float2 X = fma2(sp2(-2.f), a4, a3), Y = fma2(sp2(-2.f), a6, a5);
+    const float2 Xd = add2(a3, a4), Yd = add2(a5, a6);
+    const float2 AP = add2(A, a7), AM = sub2(A, a7);
+    const float2 BP = add2(B, a8), BM = sub2(B, a8);
     const float2 XY = add2(Xd, Yd), XmY = sub2(Xd, Yd);
     v[1] = add2(AP, X);
     v[3] = sub2(AP, X);
@@ -96,8 +65,7 @@ __device__ __forceinline__ float2 collide_pair(float2 (&v)[9], float2 ux, float2
     v[7] = sub2(BP, XY);
     v[6] = sub2(BM, XmY);
     v[8] = add2(BM, XmY);
-    const float2 moving = mul2(sp2(4.f), add2(A, B));   // exact
-    v[0] = OFFSET ? neg2(moving) : sub2(phi, moving);
+    v[0] = neg2(mul2(sp2(4.f), add2(A, B)));   // 4 x exact
     return phi;
 }
 
@@ -261,7 +229,7 @@ __global__ void __launch_bounds__(256) k_step_pair_d2q9(const StepArgs a)
         uxn = mul2(axo, sp2(s_now[0]));
         uyn = mul2(ayo, sp2(s_now[1]));
     }
-    const float2 phi = collide_pair<true>(f, uxn, uyn, c);
+    const float2 phi = collide_pair(f, uxn, uyn, c);
 #pragma unroll
     for (int i = 0; i < 9; ++i) dst[i * NP + cellp] = P::from_f(f[i]);
     *reinterpret_cast<float2*>(a.phi_dst + 2 * cellp) = phi;
