@@ -291,9 +291,13 @@ typedef struct {
 } lbm_cde_channel_desc;
 
 typedef struct {
-    int32_t mode;            /* LBM_BATCH_AUTO (persistent until autotuned) / PERSISTENT / PER_STEP */
-    int32_t tile_rows;       /* rows per work tile (a tile is 32 columns x tile_rows rows, one
-                                warp), 1 .. 1024; default 16 */
+    int32_t mode;            /* LBM_BATCH_AUTO (persistent until autotuned) / PERSISTENT (one
+                                cooperative launch per graph chunk, warps walk 32-column row
+                                strips, a bounded grid barrier between steps) / PER_STEP (per
+                                step: one thread per node in 32 x 8 blocks, then two moment
+                                passes) */
+    int32_t tile_rows;       /* PERSISTENT: rows per work tile (a tile is 32 columns x tile_rows
+                                rows, one warp), 1 .. 1024; default 16 */
     int32_t graph_steps;     /* steps per captured CUDA graph (ring of moments), 1 .. 4096 */
     int64_t barrier_timeout_cycles; /* clock64 cycles a CTA waits at a grid barrier before the
                                 launch gives up with LBM_E_TIMEOUT (default 2e9, about 1 s) */
@@ -326,7 +330,7 @@ lbm_status lbm_cde_batch_get_phi(lbm_cde_batch_t b, float* phi_dev);
  * then invalid until the next set_phi). */
 lbm_status lbm_cde_batch_run(lbm_cde_batch_t b, int64_t nsteps, double* moments_host);
 
-/* Times every execution mode x tile height (8, 16, 32 rows) on `steps` steps,
+/* Times PERSISTENT at tile heights 8, 16, 32 rows and PER_STEP on `steps` steps,
  * keeps the fastest (restoring the state and step count) and reports it. */
 lbm_status lbm_cde_batch_autotune(lbm_cde_batch_t b, int64_t steps, int32_t* mode_out, int32_t* tile_out);
 

@@ -41,6 +41,39 @@ struct InstDev {
     double vref;          // reference drift per step
     const float* urow;    // [2][ny] or nullptr
     Coef c;
+    int tx, tyc;          // 32 x 8 cell tiles of the PER_STEP kernel: columns, rows of tiles
+    long long ctile0;     // first cell tile of this instance
+    long long cblk0, ncblk;   // 256-column blocks of the moment pass
+};
+
+// PER_STEP mode: one thread per node, one 32 x 8 block per cell tile; the
+// instance constants travel in the kernel parameters (warp-uniform reads from
+// the constant bank), so the collision holds no coefficient registers.
+struct CK {               // the constants collide<D2Q9> reads
+    float meq1, meq2, b1, b2, g7, g8;
+    float s[9];
+    float A[4], C[4];
+};
+
+struct InstK {
+    long long off;        // first cell of the instance
+    const float* urow;
+    int nx, ny, tx;       // tx: column tiles
+    int tile0;            // first cell tile of the instance within its launch
+    int bc_lo, bc_hi;
+    CK c;
+};
+
+constexpr int CELL_INST = 160;   // instances per launch (kernel parameters < 32 KB)
+
+struct CellArgs {
+    float* buf[2];
+    const long long* kdev;
+    float* strip;         // [cell tiles][32] column sums of w_y phi over each tile's 8 rows
+    long long ncat;
+    int ninst;            // instances of this launch
+    int tile_base;        // first cell tile of this launch
+    InstK inst[CELL_INST];
 };
 
 struct TileDev {
@@ -250,89 +283,137 @@ __global__ void __launch_bounds__(256, 4) k_batch_persistent(const BatchArgs a)
     }
 }
 
-// Cell-parallel step for PER_STEP mode: one block of 32 x 8 threads per tile,
-// every thread one node (rows y0 + warp, +8, ...), so each thread has all nine
-// pulls in flight at once; the column sums of the strip meet in shared memory.
-__global__ void __launch_bounds__(256) k_batch_step_cells(const BatchArgs a)
+// PER_STEP mode step: block t is cell tile t of this launch (32 columns x 8
+// rows of one instance); every thread pulls, collides and stores one node, and
+// warp 0 writes the tile's 32 column sums of w_y phi.
+template <typename IX>
+__global__ void __launch_bounds__(256) k_batch_cells(const __grid_constant__ CellArgs a)
 {
-    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
-    const long long t = blockIdx.x;
-    const long long k = *a.kdev + 1;
-    const float* __restrict__ src = a.buf[(k - 1) & 1];
-    float* __restrict__ dst = a.buf[k & 1];
-    const TileDev td = a.tiles[t];
-    const InstDev& I = a.inst[td.inst];
-    const Coef& cs = I.c;
+    const int t = blockIdx.x;
+    int lo = 0, hi = a.ninst - 1;        // instance holding tile t (tile0 ascends)
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.inst[mid].tile0 <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const InstK& I = a.inst[lo];
     const int nx = I.nx, ny = I.ny;
-    const long long N = a.ncat;
-    const int x = td.x0 + lane;
-    const bool live = x < nx;
-    const int xc = live ? x : nx - 1;
+    const int lt = t - I.tile0, ty = lt / I.tx;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int x = (lt - ty * I.tx) * 32 + lane, y = ty * 8 + wy;
+    const bool live = x < nx && y < ny;
+    const int xc = min(x, nx - 1), yc = min(y, ny - 1);
+    const long long k = *a.kdev + 1;
+    const float* __restrict__ src = a.buf[(k - 1) & 1] + I.off;
+    float* __restrict__ dst = a.buf[k & 1] + I.off;
+    const IX N = (IX)a.ncat;
     const int xs[3] = {xc + 1 == nx ? 0 : xc + 1, xc, xc == 0 ? nx - 1 : xc - 1};
-    const long long base = I.off;
+    const int ys[3] = {yc + 1 == ny ? 0 : yc + 1, yc, yc == 0 ? ny - 1 : yc - 1};
+    float f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        f[i] = __ldg(src + ((IX)i * N + (IX)ys[D2Q9::ey(i) + 1] * nx + xs[D2Q9::ex(i) + 1]));
     const bool walls = I.bc_lo != BC_PERIODIC;
-    float col = 0.f;
-    for (int y = td.y0 + wy; y < td.y1; y += 8) {
-        const int ys[3] = {y + 1 == ny ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};
-        float f[9];
+    const bool lo_w = walls && yc == 0, hi_w = walls && yc == ny - 1;
+    if (lo_w || hi_w) {
+        const int kind = lo_w ? I.bc_lo : I.bc_hi;
+        const IX cell = (IX)yc * nx + xc;
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            f[i] = __ldg(src + (long long)i * N + base + (long long)ys[D2Q9::ey(i) + 1] * nx + xs[D2Q9::ex(i) + 1]);
-        const bool lo = walls && y == 0;
-        const bool hi = walls && y == ny - 1;
-        if (lo || hi) {
-            const int kind = lo ? I.bc_lo : I.bc_hi;
-            const long long cell = base + (long long)y * nx + xc;
-#pragma unroll
-            for (int i = 0; i < 9; ++i)
-                if (D2Q9::ey(i) != 0 && ((D2Q9::ey(i) == 1) == lo)) {
-                    if (kind == BC_BOUNCE) f[i] = __ldg(src + (long long)opposite<D2Q9>(i) * N + cell);
-                    else f[i] = f[mirror_y<D2Q9>(i)];
-                }
-        }
-        float ux = 0.f, uy = 0.f;
-        if (I.urow) {
-            ux = __ldg(I.urow + y);
-            uy = __ldg(I.urow + ny + y);
-        }
-        const float phi = collide<D2Q9>(f, ux, uy, 0.f, cs);
-        if (live) {
-            const long long cell = base + (long long)y * nx + x;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) dst[(long long)i * N + cell] = f[i];
-        }
-        col += (walls && (y == 0 || y == ny - 1)) ? 0.5f * phi : phi;
+            if (D2Q9::ey(i) != 0 && ((D2Q9::ey(i) == 1) == lo_w)) {
+                if (kind == BC_BOUNCE) f[i] = __ldg(src + ((IX)opposite<D2Q9>(i) * N + cell));
+                else f[i] = f[mirror_y<D2Q9>(i)];
+            }
     }
-    __shared__ float cols[8][32];
-    cols[wy][lane] = col;
+    float ux = 0.f, uy = 0.f;
+    if (I.urow) {
+        ux = __ldg(I.urow + yc);
+        uy = __ldg(I.urow + ny + yc);
+    }
+    const float phi = collide<D2Q9, false, CK>(f, ux, uy, 0.f, I.c);
+    if (live) {
+        const IX cell = (IX)y * nx + x;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dst[(IX)i * N + cell] = f[i];
+    }
+    __shared__ float cs[8][32];
+    cs[wy][lane] = live ? ((lo_w || hi_w) ? __fmul_rn(0.5f, phi) : phi) : 0.f;
     __syncthreads();
-    if (wy != 0) return;
-    double pb = 0.0;
+    if (wy == 0) {
+        float sum = cs[0][lane];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) pb += (double)cols[r][lane];
-    if (!live) pb = 0.0;
-    const long long cref = I.xref0 + (long long)llround(I.vref * (double)k);
-    long long xi = wrap_ll((long long)x - cref, nx);
-    if (xi >= (nx + 1) / 2) xi -= nx;
-    double m0 = pb, m1 = pb * (double)xi, m2 = pb * (double)xi * (double)xi;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        m0 += __shfl_down_sync(0xffffffffu, m0, off);
-        m1 += __shfl_down_sync(0xffffffffu, m1, off);
-        m2 += __shfl_down_sync(0xffffffffu, m2, off);
-    }
-    if (lane == 0) {
-        double* part = a.partials + (long long)(k & 1) * a.ntiles * 3;
-        part[t * 3 + 0] = m0;
-        part[t * 3 + 1] = m1;
-        part[t * 3 + 2] = m2;
+        for (int r = 1; r < 8; ++r) sum += cs[r][lane];
+        a.strip[(long long)(a.tile_base + t) * 32 + lane] = sum;
     }
 }
 
-__global__ void __launch_bounds__(256) k_batch_moments(const BatchArgs a)
+// Eq. 47 moments of step k for PER_STEP mode, two deterministic passes.
+// Pass 1: one thread per column x of an instance (256-column blocks, each
+// within one instance): phi-bar(x) = FP64 sum of the column's tile sums, then
+// phi-bar {1, xi, xi^2}, reduced over the block in a fixed tree to one partial.
+// Pass 2: one warp per instance adds its block partials in index order.
+__global__ void __launch_bounds__(256) k_batch_col_moments(const BatchArgs a, const float* __restrict__ strip,
+                                                           const int* __restrict__ cblk_inst,
+                                                           double* __restrict__ cpart)
 {
+    const int blk = blockIdx.x;
+    const int i = cblk_inst[blk];
+    const InstDev& I = a.inst[i];
     const long long k = *a.kdev + 1;
-    reduce_moments(a, k, a.partials + (long long)(k & 1) * a.ntiles * 3);
+    const long long cref = I.xref0 + (long long)llround(I.vref * (double)k);
+    const int nx = I.nx;
+    const int x = (blk - (int)I.cblk0) * 256 + threadIdx.x;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    if (x < nx) {
+        const float* p = strip + (I.ctile0 + (x >> 5)) * 32 + (x & 31);
+        const long long step = (long long)I.tx * 32;
+        double pb = 0.0;
+        for (int ty = 0; ty < I.tyc; ++ty) pb += (double)p[ty * step];
+        long long xi = wrap_ll((long long)x - cref, nx);
+        if (xi >= (nx + 1) / 2) xi -= nx;
+        const double xd = (double)xi;
+        s0 = pb;
+        s1 = pb * xd;
+        s2 = s1 * xd;
+    }
+    __shared__ double r[3][256];
+    r[0][threadIdx.x] = s0;
+    r[1][threadIdx.x] = s1;
+    r[2][threadIdx.x] = s2;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int j = 0; j < 3; ++j) r[j][threadIdx.x] += r[j][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) cpart[(long long)blk * 3 + threadIdx.x] = r[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(256) k_batch_inst_moments(const BatchArgs a, const double* __restrict__ cpart)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    if (i >= a.ninst) return;
+    const InstDev& I = a.inst[i];
+    const long long k = *a.kdev + 1;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (long long b = I.cblk0 + lane; b < I.cblk0 + I.ncblk; b += 32) {
+        s0 += cpart[b * 3 + 0];
+        s1 += cpart[b * 3 + 1];
+        s2 += cpart[b * 3 + 2];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, off);
+        s1 += __shfl_down_sync(0xffffffffu, s1, off);
+        s2 += __shfl_down_sync(0xffffffffu, s2, off);
+    }
+    if (lane == 0) {
+        double* out = a.moments + (((k - 1) % a.ring) * a.ninst + i) * 3;
+        out[0] = s0;
+        out[1] = s1;
+        out[2] = s2;
+    }
 }
 
 __global__ void k_batch_advance(long long* kdev, int n)
@@ -373,6 +454,8 @@ __global__ void k_batch_phi(const float* __restrict__ f, long long ncat, float* 
 }
 
 static cudaError_t launch_mode(int mode, const BatchArgs& a, int grid_persistent, long long* kdev,
+                               const std::vector<CellArgs>& cells, const std::vector<int>& cell_tiles,
+                               const float* strip, const int* cblk_inst, int ncblk, double* cpart,
                                cudaStream_t st)
 {
     if (mode == LBM_BATCH_PERSISTENT) {
@@ -386,10 +469,15 @@ static cudaError_t launch_mode(int mode, const BatchArgs& a, int grid_persistent
         k_batch_advance<<<1, 1, 0, st>>>(kdev, a.nsteps);
         return cudaGetLastError();
     }
-    const unsigned nbm = (unsigned)((a.ninst + 7) / 8);
+    // 32-bit offsets when the last plane offset 9 ncat fits in 31 bits
+    const bool i32 = 9LL * a.ncat < (1LL << 31);
     for (int s = 0; s < a.nsteps; ++s) {
-        k_batch_step_cells<<<(unsigned)a.ntiles, 256, 0, st>>>(a);
-        k_batch_moments<<<nbm, 256, 0, st>>>(a);
+        for (size_t g = 0; g < cells.size(); ++g) {
+            if (i32) k_batch_cells<int><<<(unsigned)cell_tiles[g], 256, 0, st>>>(cells[g]);
+            else k_batch_cells<long long><<<(unsigned)cell_tiles[g], 256, 0, st>>>(cells[g]);
+        }
+        k_batch_col_moments<<<(unsigned)ncblk, 256, 0, st>>>(a, strip, cblk_inst, cpart);
+        k_batch_inst_moments<<<(unsigned)((a.ninst + 7) / 8), 256, 0, st>>>(a, cpart);
         k_batch_advance<<<1, 1, 0, st>>>(kdev, 1);
     }
     return cudaGetLastError();
@@ -432,6 +520,12 @@ struct lbm_cde_batch_s {
     int graph_key[2] = {-1, -1};
     bool use_graph = true;
     double* stage = nullptr;       // pinned host staging for one chunk of moments
+    std::vector<lbm::CellArgs> cells;   // PER_STEP launches (instances in groups of CELL_INST)
+    std::vector<int> cell_tiles;        // cell tiles of each launch
+    float* strip = nullptr;             // [cell tiles][32] column sums
+    int* cblk_inst = nullptr;           // instance of each 256-column block of the moment pass
+    int ncblk = 0;
+    double* cpart = nullptr;            // [ncblk][3] moment partials
     cudaStream_t st = nullptr;
     std::string err;
 };
@@ -529,7 +623,8 @@ static lbm::BatchArgs batch_args(lbm_cde_batch_t b, int nsteps)
 
 static cudaError_t launch_batch(lbm_cde_batch_t b, const lbm::BatchArgs& a)
 {
-    return lbm::launch_mode(b->mode, a, lbm::persistent_grid(), b->kdev, b->st);
+    return lbm::launch_mode(b->mode, a, lbm::persistent_grid(), b->kdev, b->cells, b->cell_tiles, b->strip,
+                            b->cblk_inst, b->ncblk, b->cpart, b->st);
 }
 
 static void drop_graph(lbm_cde_batch_t b)
@@ -679,18 +774,75 @@ lbm_status lbm_cde_batch_create(const lbm_cde_channel_desc* descs, int32_t n, co
         I.vref = d.x_ref_velocity;
         I.urow = d.u_row_dev;
         batch_coef(d, A, I.c);
+        I.tx = (I.nx + 31) / 32;
+        I.tyc = (I.ny + 7) / 8;
+        I.ctile0 = i ? b->inst[i - 1].ctile0 + (long long)b->inst[i - 1].tx * b->inst[i - 1].tyc : 0;
+        I.ncblk = (I.nx + 255) / 256;
+        I.cblk0 = i ? b->inst[i - 1].cblk0 + b->inst[i - 1].ncblk : 0;
         off += d.nx * d.ny;
     }
     b->ncat = off;
+    const long long ncell_tiles = b->inst[n - 1].ctile0 + (long long)b->inst[n - 1].tx * b->inst[n - 1].tyc;
+    if (ncell_tiles >= (1LL << 31) - 1) {
+        delete b;
+        return bfail(nullptr, LBM_E_ARG, "batch too large");
+    }
     b->inst_dev = static_cast<lbm::InstDev*>(balloc(b, sizeof(lbm::InstDev) * n));
     for (int p = 0; p < 2; ++p) b->buf[p] = static_cast<float*>(balloc(b, sizeof(float) * 9 * (size_t)off));
     b->sync = static_cast<unsigned*>(balloc(b, 64));
     b->status = reinterpret_cast<int*>(b->sync + 4);
     b->kdev = reinterpret_cast<long long*>(b->sync + 6);
     b->moments = static_cast<double*>(balloc(b, sizeof(double) * 3 * (size_t)n * b->chunk));
-    if (!b->inst_dev || !b->buf[0] || !b->buf[1] || !b->sync || !b->moments) {
+    b->strip = static_cast<float*>(balloc(b, sizeof(float) * 32 * (size_t)ncell_tiles));
+    b->ncblk = (int)(b->inst[n - 1].cblk0 + b->inst[n - 1].ncblk);
+    b->cblk_inst = static_cast<int*>(balloc(b, sizeof(int) * (size_t)b->ncblk));
+    b->cpart = static_cast<double*>(balloc(b, sizeof(double) * 3 * (size_t)b->ncblk));
+    if (!b->inst_dev || !b->buf[0] || !b->buf[1] || !b->sync || !b->moments || !b->strip || !b->cblk_inst ||
+        !b->cpart) {
         lbm_cde_batch_destroy(b);
         return bfail(nullptr, LBM_E_OOM, "batch allocation failed");
+    }
+    {
+        std::vector<int> ci((size_t)b->ncblk);
+        for (int i = 0; i < n; ++i)
+            for (long long q = 0; q < b->inst[i].ncblk; ++q) ci[(size_t)(b->inst[i].cblk0 + q)] = i;
+        cudaMemcpyAsync(b->cblk_inst, ci.data(), sizeof(int) * ci.size(), cudaMemcpyHostToDevice, b->st);
+        cudaStreamSynchronize(b->st);
+    }
+    // PER_STEP launches: instances in groups of CELL_INST, constants by value
+    for (int g0 = 0; g0 < n; g0 += lbm::CELL_INST) {
+        lbm::CellArgs ca{};
+        ca.buf[0] = b->buf[0];
+        ca.buf[1] = b->buf[1];
+        ca.kdev = b->kdev;
+        ca.strip = b->strip;
+        ca.ncat = b->ncat;
+        ca.ninst = std::min(lbm::CELL_INST, n - g0);
+        ca.tile_base = (int)b->inst[g0].ctile0;
+        long long tiles = 0;
+        for (int j = 0; j < ca.ninst; ++j) {
+            const lbm::InstDev& I = b->inst[g0 + j];
+            lbm::InstK& K = ca.inst[j];
+            K.off = I.off;
+            K.urow = I.urow;
+            K.nx = I.nx;
+            K.ny = I.ny;
+            K.tx = I.tx;
+            K.tile0 = (int)(I.ctile0 - ca.tile_base);
+            K.bc_lo = I.bc_lo;
+            K.bc_hi = I.bc_hi;
+            K.c.meq1 = I.c.meq1;
+            K.c.meq2 = I.c.meq2;
+            K.c.b1 = I.c.b1;
+            K.c.b2 = I.c.b2;
+            K.c.g7 = I.c.g7;
+            K.c.g8 = I.c.g8;
+            for (int q = 0; q < 9; ++q) K.c.s[q] = I.c.s[q];
+            for (int q = 0; q < 4; ++q) K.c.A[q] = I.c.A[q], K.c.C[q] = I.c.C[q];
+            tiles += (long long)I.tx * I.tyc;
+        }
+        b->cells.push_back(ca);
+        b->cell_tiles.push_back((int)tiles);
     }
     cudaMemsetAsync(b->sync, 0, 64, b->st);
     lbm_status s = rebuild_tiles(b);
@@ -715,6 +867,9 @@ lbm_status lbm_cde_batch_destroy(lbm_cde_batch_t b)
     bfree(b, b->buf[1]);
     bfree(b, b->sync);
     bfree(b, b->moments);
+    bfree(b, b->strip);
+    bfree(b, b->cblk_inst);
+    bfree(b, b->cpart);
     delete b;
     return LBM_OK;
 }
@@ -813,6 +968,7 @@ lbm_status lbm_cde_batch_autotune(lbm_cde_batch_t b, int64_t steps, int32_t* mod
     cudaEventCreate(&e1);
     for (int m : modes)
         for (int tw : tws) {
+            if (m == LBM_BATCH_PER_STEP && tw != tws[0]) continue;   // fixed 32 x 8 cell tiles
             b->mode = m;
             if (b->rows != tw) {
                 b->rows = tw;

@@ -285,9 +285,9 @@ __device__ __forceinline__ float populations(const float (&a)[L::Q], float (&v)[
 // (OFFSET = true, the 16-bit storage forms), computed in moment space as
 // g = M^-1 (m' - m^eq_lin). Returns phi = m_0.
 // ---------------------------------------------------------------------------
-template <class L, bool OFFSET = false>
+template <class L, bool OFFSET = false, class CC = Coef>
 __device__ __forceinline__ float collide(float (&f)[L::Q], float ux, float uy, float uz,
-                                         const Coef& c)
+                                         const CC& c)
 {
     constexpr int Q = L::Q;
     float m[Q];
