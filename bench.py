@@ -45,7 +45,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-STEP_SOURCES = ["lbm_internal.cuh", "lbm_device.cuh", "lbm_step_inst.cuh", "step_d2q9_f32.cu",
+STEP_SOURCES = ["lbm_internal.cuh", "lbm_device.cuh", "lbm_pair.cuh", "lbm_step_inst.cuh", "step_d2q9_f32.cu",
                 "step_d2q9_f16.cu", "step_d2q9_bf16.cu"]
 
 
