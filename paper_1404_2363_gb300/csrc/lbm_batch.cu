@@ -15,7 +15,7 @@
 //   PERSISTENT : one cooperative launch runs K steps; warps take tiles from an
 //                atomic counter, and a grid barrier (bounded spin, then
 //                LBM_E_TIMEOUT) separates the steps;
-//   PER_STEP   : one launch per step (one 32 x 8 block per tile, one node per
+//   PER_STEP   : one launch per step (one 32 x 16 block per tile, two nodes per
 //                thread) plus one moment-reduction launch.
 // Either is captured once into a CUDA graph of K steps and replayed.
 #include <algorithm>
@@ -29,6 +29,7 @@
 
 #include "../../include/lbm_cde.h"
 #include "lbm_device.cuh"
+#include "lbm_pair.cuh"
 
 namespace lbm {
 
@@ -41,12 +42,12 @@ struct InstDev {
     double vref;          // reference drift per step
     const float* urow;    // [2][ny] or nullptr
     Coef c;
-    int tx, tyc;          // 32 x 8 cell tiles of the PER_STEP kernel: columns, rows of tiles
+    int tx, tyc;          // 32 x 16 cell tiles of the PER_STEP kernel: columns, rows of tiles
     long long ctile0;     // first cell tile of this instance
     long long cblk0, ncblk;   // 256-column blocks of the moment pass
 };
 
-// PER_STEP mode: one thread per node, one 32 x 8 block per cell tile; the
+// PER_STEP mode: two nodes per thread, one 32 x 16 cell tile per block; the
 // instance constants travel in the kernel parameters (warp-uniform reads from
 // the constant bank), so the collision holds no coefficient registers.
 struct CK {               // the constants collide<D2Q9> reads
@@ -69,7 +70,7 @@ constexpr int CELL_INST = 160;   // instances per launch (kernel parameters < 32
 struct CellArgs {
     float* buf[2];
     const long long* kdev;
-    float* strip;         // [cell tiles][32] column sums of w_y phi over each tile's 8 rows
+    float* strip;         // [cell tiles][32] column sums of w_y phi over each tile's 16 rows
     long long ncat;
     int ninst;            // instances of this launch
     int tile_base;        // first cell tile of this launch
@@ -283,9 +284,10 @@ __global__ void __launch_bounds__(256, 4) k_batch_persistent(const BatchArgs a)
     }
 }
 
-// PER_STEP mode step: block t is cell tile t of this launch (32 columns x 8
-// rows of one instance); every thread pulls, collides and stores one node, and
-// warp 0 writes the tile's 32 column sums of w_y phi.
+// PER_STEP mode step: block t is cell tile t of this launch (32 columns x 16
+// rows of one instance). A thread owns the nodes (x, y) and (x, y + 8) and
+// evaluates both collisions in paired FP32 arithmetic (lbm_pair.cuh); warp 0
+// writes the tile's 32 column sums of w_y phi.
 template <typename IX>
 __global__ void __launch_bounds__(256) k_batch_cells(const __grid_constant__ CellArgs a)
 {
@@ -300,44 +302,62 @@ __global__ void __launch_bounds__(256) k_batch_cells(const __grid_constant__ Cel
     const int nx = I.nx, ny = I.ny;
     const int lt = t - I.tile0, ty = lt / I.tx;
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
-    const int x = (lt - ty * I.tx) * 32 + lane, y = ty * 8 + wy;
-    const bool live = x < nx && y < ny;
-    const int xc = min(x, nx - 1), yc = min(y, ny - 1);
+    const int x = (lt - ty * I.tx) * 32 + lane;
+    const int y[2] = {ty * 16 + wy, ty * 16 + 8 + wy};
+    const bool xlive = x < nx;
+    const bool live[2] = {xlive && y[0] < ny, xlive && y[1] < ny};
+    const int xc = min(x, nx - 1);
+    const int yc[2] = {min(y[0], ny - 1), min(y[1], ny - 1)};
     const long long k = *a.kdev + 1;
     const float* __restrict__ src = a.buf[(k - 1) & 1] + I.off;
     float* __restrict__ dst = a.buf[k & 1] + I.off;
     const IX N = (IX)a.ncat;
     const int xs[3] = {xc + 1 == nx ? 0 : xc + 1, xc, xc == 0 ? nx - 1 : xc - 1};
-    const int ys[3] = {yc + 1 == ny ? 0 : yc + 1, yc, yc == 0 ? ny - 1 : yc - 1};
-    float f[9];
+    float f[2][9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-        f[i] = __ldg(src + ((IX)i * N + (IX)ys[D2Q9::ey(i) + 1] * nx + xs[D2Q9::ex(i) + 1]));
-    const bool walls = I.bc_lo != BC_PERIODIC;
-    const bool lo_w = walls && yc == 0, hi_w = walls && yc == ny - 1;
-    if (lo_w || hi_w) {
-        const int kind = lo_w ? I.bc_lo : I.bc_hi;
-        const IX cell = (IX)yc * nx + xc;
+    for (int h = 0; h < 2; ++h) {
+        const int ys[3] = {yc[h] + 1 == ny ? 0 : yc[h] + 1, yc[h], yc[h] == 0 ? ny - 1 : yc[h] - 1};
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            if (D2Q9::ey(i) != 0 && ((D2Q9::ey(i) == 1) == lo_w)) {
-                if (kind == BC_BOUNCE) f[i] = __ldg(src + ((IX)opposite<D2Q9>(i) * N + cell));
-                else f[i] = f[mirror_y<D2Q9>(i)];
-            }
+            f[h][i] = __ldg(src + ((IX)i * N + (IX)ys[D2Q9::ey(i) + 1] * nx + xs[D2Q9::ex(i) + 1]));
     }
-    float ux = 0.f, uy = 0.f;
-    if (I.urow) {
-        ux = __ldg(I.urow + yc);
-        uy = __ldg(I.urow + ny + yc);
-    }
-    const float phi = collide<D2Q9, false, CK>(f, ux, uy, 0.f, I.c);
-    if (live) {
-        const IX cell = (IX)y * nx + x;
+    const bool walls = I.bc_lo != BC_PERIODIC;
+    bool wall[2] = {false, false};
 #pragma unroll
-        for (int i = 0; i < 9; ++i) dst[(IX)i * N + cell] = f[i];
+    for (int h = 0; h < 2; ++h) {
+        const bool lo_w = walls && yc[h] == 0, hi_w = walls && yc[h] == ny - 1;
+        wall[h] = lo_w || hi_w;
+        if (lo_w || hi_w) {
+            const int kind = lo_w ? I.bc_lo : I.bc_hi;
+            const IX cell = (IX)yc[h] * nx + xc;
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                if (D2Q9::ey(i) != 0 && ((D2Q9::ey(i) == 1) == lo_w)) {
+                    if (kind == BC_BOUNCE) f[h][i] = __ldg(src + ((IX)opposite<D2Q9>(i) * N + cell));
+                    else f[h][i] = f[h][mirror_y<D2Q9>(i)];
+                }
+        }
     }
+    float2 ux = sp2(0.f), uy = sp2(0.f);
+    if (I.urow) {
+        ux = make_float2(__ldg(I.urow + yc[0]), __ldg(I.urow + yc[1]));
+        uy = make_float2(__ldg(I.urow + ny + yc[0]), __ldg(I.urow + ny + yc[1]));
+    }
+    float2 v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = make_float2(f[0][i], f[1][i]);
+    const float2 phi = collide_pair_f32(v, ux, uy, I.c);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (live[h]) {
+            const IX cell = (IX)y[h] * nx + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) dst[(IX)i * N + cell] = h ? v[i].y : v[i].x;
+        }
     __shared__ float cs[8][32];
-    cs[wy][lane] = live ? ((lo_w || hi_w) ? __fmul_rn(0.5f, phi) : phi) : 0.f;
+    const float pa = live[0] ? (wall[0] ? __fmul_rn(0.5f, phi.x) : phi.x) : 0.f;
+    const float pb = live[1] ? (wall[1] ? __fmul_rn(0.5f, phi.y) : phi.y) : 0.f;
+    cs[wy][lane] = pa + pb;
     __syncthreads();
     if (wy == 0) {
         float sum = cs[0][lane];
@@ -775,7 +795,7 @@ lbm_status lbm_cde_batch_create(const lbm_cde_channel_desc* descs, int32_t n, co
         I.urow = d.u_row_dev;
         batch_coef(d, A, I.c);
         I.tx = (I.nx + 31) / 32;
-        I.tyc = (I.ny + 7) / 8;
+        I.tyc = (I.ny + 15) / 16;
         I.ctile0 = i ? b->inst[i - 1].ctile0 + (long long)b->inst[i - 1].tx * b->inst[i - 1].tyc : 0;
         I.ncblk = (I.nx + 255) / 256;
         I.cblk0 = i ? b->inst[i - 1].cblk0 + b->inst[i - 1].ncblk : 0;
@@ -968,7 +988,7 @@ lbm_status lbm_cde_batch_autotune(lbm_cde_batch_t b, int64_t steps, int32_t* mod
     cudaEventCreate(&e1);
     for (int m : modes)
         for (int tw : tws) {
-            if (m == LBM_BATCH_PER_STEP && tw != tws[0]) continue;   // fixed 32 x 8 cell tiles
+            if (m == LBM_BATCH_PER_STEP && tw != tws[0]) continue;   // fixed 32 x 16 cell tiles
             b->mode = m;
             if (b->rows != tw) {
                 b->rows = tw;

@@ -69,6 +69,74 @@ __device__ __forceinline__ float2 collide_pair(float2 (&v)[9], float2 ux, float2
     return phi;
 }
 
+// collide<D2Q9, false> for two nodes: post-collision populations, with the
+// u^2 terms of MRT-B1/B2. CC is any constants type with the fields collide reads.
+template <class CC>
+__device__ __forceinline__ float2 collide_pair_f32(float2 (&v)[9], float2 ux, float2 uy, const CC& c)
+{
+    const float2 sx = add2(v[1], v[3]), ax = sub2(v[1], v[3]);
+    const float2 sy = add2(v[2], v[4]), ay = sub2(v[2], v[4]);
+    const float2 p57 = add2(v[5], v[7]), d57 = sub2(v[5], v[7]);
+    const float2 p68 = add2(v[6], v[8]), d68 = sub2(v[6], v[8]);
+    const float2 sa = add2(sx, sy), sd = add2(p57, p68);
+    const float2 jx = sub2(d57, d68), jy = add2(d57, d68);
+    const float2 phi = add2(add2(v[0], sa), sd);
+    const float2 m1 = fma2(sp2(2.f), sd, fma2(sp2(-4.f), v[0], neg2(sa)));
+    const float2 m2 = fma2(sp2(-2.f), sa, fma2(sp2(4.f), v[0], sd));
+    const float2 m3 = add2(ax, jx), m4 = fma2(sp2(-2.f), ax, jx);
+    const float2 m5 = add2(ay, jy), m6 = fma2(sp2(-2.f), ay, jy);
+    const float2 m7 = sub2(sx, sy), m8 = sub2(p57, p68);
+    // d = m - m^eq (Eq. 15 with the MRT-B1/B2 u^2 terms when present)
+    float2 d1 = fma2(sp2(-c.meq1), phi, m1), d2 = fma2(sp2(-c.meq2), phi, m2);
+    const float2 d3 = fma2(neg2(phi), ux, m3), d4 = fma2(phi, ux, m4);
+    const float2 d5 = fma2(neg2(phi), uy, m5), d6 = fma2(phi, uy, m6);
+    float2 d7 = m7, d8 = m8;
+    if (c.b1 != 0.f || c.b2 != 0.f || c.g7 != 0.f || c.g8 != 0.f) {
+        const float2 uyy = mul2(uy, uy);
+        const float2 u2 = fma2(ux, ux, uyy);
+        d1 = fma2(mul2(sp2(-c.b1), u2), phi, d1);
+        d2 = fma2(mul2(sp2(-c.b2), u2), phi, d2);
+        d7 = fma2(mul2(sp2(-c.g7), fma2(ux, ux, neg2(uyy))), phi, d7);
+        d8 = fma2(mul2(sp2(-c.g8), mul2(ux, uy)), phi, d8);
+    }
+    // m' = m - S d (Eq. 31), scaled by 1/|M_k|^2
+    float2 r0 = fma2(sp2(c.A[0]), d3, sp2(0.f));
+    r0 = fma2(sp2(c.C[0]), d4, r0);
+    r0 = fma2(sp2(c.A[1]), d5, r0);
+    r0 = fma2(sp2(c.C[1]), d6, r0);
+    float2 r1 = fma2(sp2(c.A[2]), d3, sp2(0.f));
+    r1 = fma2(sp2(c.C[2]), d4, r1);
+    r1 = fma2(sp2(c.A[3]), d5, r1);
+    r1 = fma2(sp2(c.C[3]), d6, r1);
+    const float2 a0 = mul2(phi, sp2(1.f / 9.f));
+    const float2 a1 = mul2(fma2(sp2(-c.s[1]), d1, m1), sp2(1.f / 36.f));
+    const float2 a2 = mul2(fma2(sp2(-c.s[2]), d2, m2), sp2(1.f / 36.f));
+    const float2 a3 = mul2(sub2(m3, r0), sp2(1.f / 6.f));
+    const float2 a4 = mul2(fma2(sp2(-c.s[4]), d4, m4), sp2(1.f / 12.f));
+    const float2 a5 = mul2(sub2(m5, r1), sp2(1.f / 6.f));
+    const float2 a6 = mul2(fma2(sp2(-c.s[6]), d6, m6), sp2(1.f / 12.f));
+    const float2 a7 = mul2(fma2(sp2(-c.s[7]), d7, m7), sp2(0.25f));
+    const float2 a8 = mul2(fma2(sp2(-c.s[8]), d8, m8), sp2(0.25f));
+    // f' = M^T a (populations<D2Q9, false, false>), rest population from the mass balance
+    const float2 A = fma2(sp2(-2.f), a2, sub2(a0, a1));
+    const float2 B = fma2(sp2(2.f), a1, add2(a0, a2));
+    const float2 X = fma2(sp2(-2.f), a4, a3), Y = fma2(sp2(-2.f), a6, a5);
+    const float2 Xd = add2(a3, a4), Yd = add2(a5, a6);
+    const float2 AP = add2(A, a7), AM = sub2(A, a7);
+    const float2 BP = add2(B, a8), BM = sub2(B, a8);
+    const float2 XY = add2(Xd, Yd), XmY = sub2(Xd, Yd);
+    v[1] = add2(AP, X);
+    v[3] = sub2(AP, X);
+    v[2] = add2(AM, Y);
+    v[4] = sub2(AM, Y);
+    v[5] = add2(BP, XY);
+    v[7] = sub2(BP, XY);
+    v[6] = sub2(BM, XmY);
+    v[8] = add2(BM, XmY);
+    v[0] = sub2(phi, mul2(sp2(4.f), add2(A, B)));
+    return phi;
+}
+
 // paired 16-bit words
 template <int S> struct Pair;
 template <> struct Pair<ST_F16> {

@@ -76,7 +76,7 @@ def test_instances_and_moments_match_oracle(O):
 
 def test_modes_and_tiles_agree():
     chs, phis = channels()
-    ref = None
+    ref, ref_ps = None, None
     for mode, tile, gsteps in [("persistent", 16, 16), ("per_step", 8, 16), ("persistent", 5, 7),
                                ("per_step", 32, 1)]:
         b = Batch(chs, mode=mode, tile_rows=tile, graph_steps=gsteps)
@@ -84,20 +84,32 @@ def test_modes_and_tiles_agree():
         mom = b.run(53)
         phi = torch.cat([g.reshape(-1) for g in b.get_phi()]).cpu().numpy()
         b.close()
+        if mode == "per_step":
+            # paired arithmetic (two nodes per thread): the same steps up to the
+            # compiler's fusing of paired multiply-adds; identical across chunkings
+            if ref_ps is None:
+                ref_ps = (mom, phi)
+            else:
+                assert np.array_equal(phi, ref_ps[1]), (mode, tile)
+                assert np.array_equal(mom, ref_ps[0]), (mode, tile)
         if ref is None:
             ref = (mom, phi)
-        else:
+        elif mode == "persistent":
             # the fields are bitwise identical; the moment sums differ only in
             # the summation order of the column sums over tile strips
             assert np.array_equal(phi, ref[1]), (mode, tile)
             assert np.abs(mom[..., 0] / ref[0][..., 0] - 1).max() < 1e-7, (mode, tile)
             assert np.abs(sigma2(mom) / sigma2(ref[0]) - 1).max() < 1e-7, (mode, tile)
+        else:
+            assert np.abs(phi - ref[1]).max() <= 1e-6 * np.abs(ref[1]).max(), (mode, tile)
+            assert np.abs(mom[..., 0] / ref[0][..., 0] - 1).max() < 1e-6, (mode, tile)
+            assert np.abs(sigma2(mom) / sigma2(ref[0]) - 1).max() < 1e-6, (mode, tile)
     b = Batch(chs)
     b.set_phi(phis)
     b.autotune(steps=16)
     b.set_phi(phis)
     mom = b.run(53)
-    assert np.abs(sigma2(mom) / sigma2(ref[0]) - 1).max() < 1e-7
+    assert np.abs(sigma2(mom) / sigma2(ref[0]) - 1).max() < 1e-6
 
 
 def test_instance_equals_standalone_solver():
