@@ -45,12 +45,11 @@ def peaks():
         return 6800.0, "fallback"
 
 
-STEP_SOURCES = ["lbm_internal.cuh", "lbm_device.cuh", "lbm_pair.cuh", "lbm_step_inst.cuh", "step_d2q9_f32.cu",
-                "step_d2q9_f16.cu", "step_d2q9_bf16.cu"]
+STEP_SOURCES = ["lbm_internal.cuh", "lbm_device.cuh", "lbm_step_inst.cuh", "step_d2q9_f32.cu"]
 
 
 def kernel_source_hash():
-    """Hash of the sources that define the D2Q9 step kernels (the profiled ones)."""
+    """Hash of the sources that define the D2Q9 FP32 step kernel (the profiled one)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1404_2363_gb300", "csrc")
     for f in STEP_SOURCES:
