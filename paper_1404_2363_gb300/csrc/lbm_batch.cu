@@ -615,6 +615,7 @@ static void batch_coef(const lbm_cde_channel_desc& d, const double A[4], lbm::Co
     c.wd = (float)(8.0 / 144.0);
     c.ka = (float)(48.0 / 144.0);
     c.kd = (float)(12.0 / 144.0);
+    c.eps0 = (float)((double)c.w0 + 4.0 * (double)c.wa + 4.0 * (double)c.wd - 1.0);
     lbm::fold_offset_coef(c);
 }
 

@@ -197,6 +197,8 @@ static void refresh_coef(lbm_cde_t h)
         c.ka = (float)(1.0 / 5.0);
         c.kd = (float)(3.0 / 40.0);
     }
+    const double na = h->q == 9 ? 4.0 : 6.0, nd = h->q == 9 ? 4.0 : 8.0;
+    c.eps0 = (float)((double)c.w0 + na * (double)c.wa + nd * (double)c.wd - 1.0);
 }
 
 static StepArgs make_args(lbm_cde_t h, int src_idx)

@@ -309,7 +309,7 @@ __device__ __forceinline__ float collide(float (&f)[L::Q], float ux, float uy, f
         a[8] = __fmul_rn(m[8], c.ro[8]);
         a[3] = fmaf(c.fr[0], dl3, fmaf(c.fr[1], dl4, fmaf(c.fr[2], dl5, __fmul_rn(c.fr[3], dl6))));
         a[5] = fmaf(c.fr[4], dl3, fmaf(c.fr[5], dl4, fmaf(c.fr[6], dl5, __fmul_rn(c.fr[7], dl6))));
-        f[0] = -populations<L, true, false>(a, f);
+        f[0] = fmaf(-c.eps0, phi, -populations<L, true, false>(a, f));
         return phi;
     }
     const float u[3] = {ux, uy, uz};
@@ -362,10 +362,12 @@ __device__ __forceinline__ float collide(float (&f)[L::Q], float ux, float uy, f
     for (int k = 0; k < Q; ++k) mp[k] = __fmul_rn(mp[k], 1.0f / (float)row_norm2<L>(k));
     const float moving = populations<L, OFFSET, false>(mp, f);
     // The rest population closes the mass balance: sum_i f'_i = m'_0 = phi
-    // (row 0 of M^-1 m'), and sum_i g_i = 0. Taking it from the moving
-    // populations keeps FP32 rounding of the 1/|M_0|^2 factor from biasing
-    // the total mass.
-    f[0] = OFFSET ? -moving : phi - moving;
+    // (row 0 of M^-1 m'). Taking it from the moving populations keeps FP32
+    // rounding of the 1/|M_0|^2 factor from biasing the total mass. For the
+    // offsets, sum_i g_i = -phi eps0 balances the FP32 weights of the decode,
+    // which sum to 1 + eps0 (else the mass would drift by phi eps0 per step).
+    if constexpr (OFFSET) f[0] = fmaf(-c.eps0, phi, -moving);   // see Coef::eps0
+    else f[0] = phi - moving;
     return phi;
 }
 

@@ -37,6 +37,10 @@ struct Coef {
     //               ((delta_r0 - A_r0) / 6, -C_r0 / 6, (delta_r1 - A_r1) / 6, -C_r1 / 6)
     float ro[9];
     float fr[8];
+    // sum_i w_i - 1 with the FP32 weights the 16-bit decode adds back (w0 + 4 wa
+    // + 4 wd for D2Q9, w0 + 6 wa + 8 wd for D3Q15): the rest offset g_0 carries
+    // -phi eps0 so that decode and store conserve mass in FP32 as they do exactly
+    float eps0;
 };
 
 // Fills ro and fr from s, A and C (D2Q9; host side).

@@ -65,7 +65,7 @@ __device__ __forceinline__ float2 collide_pair(float2 (&v)[9], float2 ux, float2
     v[7] = sub2(BP, XY);
     v[6] = sub2(BM, XmY);
     v[8] = add2(BM, XmY);
-    v[0] = neg2(mul2(sp2(4.f), add2(A, B)));   // 4 x exact
+    v[0] = fma2(sp2(-c.eps0), phi, neg2(mul2(sp2(4.f), add2(A, B))));   // 4 x exact; Coef::eps0
     return phi;
 }
 
