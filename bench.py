@@ -432,6 +432,47 @@ def adjoint_cost(store: str, ms_forward: float, nsteps: int = 400):
     return out
 
 
+def inverse_gradient_cost(nsteps: int = 2000, n: int = 1024):
+    """The adjoint inverse-problem workload (1024^2 periodic, stream-function
+    velocity, 2000 steps): one gradient evaluation of L = sum (phi_N - obs)^2
+    with respect to D and phi0 (forward with sqrt(N) checkpoints + reverse
+    sweep), against the plain forward run. At this size the 37 MB state sits in
+    L2, unlike the 4096^2 measurement above."""
+    import torch
+
+    from paper_1404_2363_gb300 import workloads as W
+    from paper_1404_2363_gb300.solver import Solver
+
+    wl = W.inverse_workload(n)
+    s = Solver(nx=n, ny=n)
+    s.set_D(wl["D"])
+    s.set_velocity(torch.from_numpy(wl["u"].astype(np.float32)).cuda())
+    phi0 = torch.from_numpy(wl["phi0"].astype(np.float32)).cuda()
+    obs = phi0.clone()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    s.set_phi(phi0)
+    s.step(50)
+    s.forward_ckpt(phi0, nsteps)
+    s.backward(torch.ones_like(phi0))          # warm-up and allocation
+    torch.cuda.synchronize()
+    ev[0].record(s.stream)
+    s.set_phi(phi0)
+    s.step(nsteps)
+    ev[1].record(s.stream)
+    phiN = s.forward_ckpt(phi0, nsteps)
+    ev[2].record(s.stream)
+    s.backward(2.0 * (phiN - obs))
+    ev[3].record(s.stream)
+    torch.cuda.synchronize()
+    s.close()
+    fwd = ev[0].elapsed_time(ev[1])
+    return {"grid": [n, n], "steps": nsteps, "forward_ms": fwd,
+            "forward_ckpt_ms": ev[1].elapsed_time(ev[2]), "backward_ms": ev[2].elapsed_time(ev[3]),
+            "gradient_ms": ev[1].elapsed_time(ev[3]),
+            "ratio_gradient_vs_forward": ev[1].elapsed_time(ev[3]) / fwd,
+            "note": "dL/dD and dL/dphi0 of L = |phi_N - obs|^2; state L2-resident at this size"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -495,6 +536,7 @@ def main():
     variants["taylor_aris_batch"] = batch_bench(args.steps)
     torch.cuda.empty_cache()
     adjoint = adjoint_cost(store, ms_forward=dt / args.steps * 1e3)
+    adjoint["inverse_problem_1024"] = inverse_gradient_cost()
     e2e = e2e_run(store, args.steps)
     if rank != 0:
         barrier(world)

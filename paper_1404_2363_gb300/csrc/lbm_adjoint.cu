@@ -21,9 +21,18 @@ namespace lbm {
 template <class L>
 __host__ __device__ constexpr int ngrad() { return 2 * L::DIM * L::DIM + L::Q; }
 
-// Rows handled by one block of the adjoint kernel: the gradient partials of
-// ADJ_ROWS nodes per thread are summed in registers before the block reduction.
+// Rows handled by one block of the adjoint kernel (AdjArgs::rows): the gradient
+// partials of that many nodes per thread are summed in registers before the
+// block reduction. At most ADJ_ROWS; fewer on small grids, so that the grid
+// still fills the GPU (adjoint_rows).
 constexpr int ADJ_ROWS = 8;
+
+int adjoint_rows(long long nx, long long ny, long long nz)
+{
+    int rows = ADJ_ROWS;
+    while (rows > 1 && ((nx + 255) / 256) * ((ny + rows - 1) / rows) * nz < 152LL * 8) rows /= 2;
+    return rows;
+}
 
 template <class L, int UK, bool WALLS>
 __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArgs a)
@@ -45,9 +54,9 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
 #pragma unroll
     for (int j = 0; j < NG; ++j) g[j] = 0.f;
 
-    const int y0 = blockIdx.y * ADJ_ROWS;
+    const int y0 = blockIdx.y * a.rows;
 #pragma unroll 1
-    for (int y = y0; y < y0 + ADJ_ROWS && y < ny; ++y) {
+    for (int y = y0; y < y0 + a.rows && y < ny; ++y) {
         const int ys[3] = {y + 1 == ny ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};
         const long long cell = (long long)xc + (long long)nx * (y + (long long)ny * z);
         // pull source of population i = push target of its adjoint (recomputed
@@ -138,7 +147,7 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
                 *p += phi * (b[3 + 2 * d] - b[4 + 2 * d]) * s_now[d];
             }
         }
-        // parameter partials (FP32 per thread over its ADJ_ROWS nodes)
+        // parameter partials (FP32 per thread over its rows)
 #pragma unroll
         for (int aa = 0; aa < DIM; ++aa)
 #pragma unroll
@@ -188,25 +197,28 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
         for (int w = 0; w < nw; ++w) s += (double)red[w][threadIdx.x];
         const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
         const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
-        a.partials[threadIdx.x * nb + blk] = s;   // [NG][nblocks]: coalesced in the next pass
+        a.partials[threadIdx.x * nb + blk] = s;   // [NG][nblocks]: coalesced in the reduction
     }
 }
 
-// Deterministic two-level sum of the per-block partials ([NG][nblocks]):
-// pass 2 reduces GRAD_CHUNKS contiguous chunks of every row in parallel,
-// pass 3 adds the chunk sums in index order to the running totals.
+// Deterministic two-level sum of the per-block partials ([nslice][NG][nblocks],
+// one slice per reverse step since the last reduction): pass 2 reduces
+// GRAD_CHUNKS contiguous chunks of every row of every slice in parallel, pass 3
+// adds the chunk sums in index order to the running totals.
 constexpr int GRAD_CHUNKS = 32;
 
 __global__ void __launch_bounds__(256) k_grad_sum2(const double* __restrict__ partials, long long nblocks,
-                                                   double* __restrict__ p2)
+                                                   int ng, int nslice, double* __restrict__ p2)
 {
     const int r = blockIdx.x, j = blockIdx.y;
     const long long len = (nblocks + GRAD_CHUNKS - 1) / GRAD_CHUNKS;
     const long long b0 = r * len;
     const long long b1 = b0 + len < nblocks ? b0 + len : nblocks;
-    const double* row = partials + (long long)j * nblocks;
     double s = 0.0;
-    for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) s += row[b];
+    for (int sl = 0; sl < nslice; ++sl) {
+        const double* row = partials + ((long long)sl * ng + j) * nblocks;
+        for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) s += row[b];
+    }
     __shared__ double red[256];
     red[threadIdx.x] = s;
     __syncthreads();
@@ -266,42 +278,65 @@ __global__ void k_adjoint_seed(const float* __restrict__ g, float* __restrict__ 
     }
 }
 
-template <class L, int UK>
-static cudaError_t adj_w(bool walls, const AdjArgs& a, cudaStream_t st, long long* nblocks)
+static long long adj_blocks(const AdjArgs& a)
 {
-    dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)((a.ny + ADJ_ROWS - 1) / ADJ_ROWS), (unsigned)a.nz);
-    *nblocks = (long long)grid.x * grid.y * grid.z;
-    if (walls) k_adjoint<L, UK, true><<<grid, 256, 0, st>>>(a);
-    else k_adjoint<L, UK, false><<<grid, 256, 0, st>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return (long long)((a.nx + 255) / 256) * ((a.ny + a.rows - 1) / a.rows) * a.nz;
+}
+
+// grad_acc += the per-block partials of nslice slices starting at base, summed in a fixed order
+template <class L>
+static cudaError_t grad_reduce(const AdjArgs& a, double* base, int nslice, cudaStream_t st)
+{
     constexpr int NG = ngrad<L>();
-    double* p2 = a.partials + *nblocks * NG;
-    k_grad_sum2<<<dim3(GRAD_CHUNKS, NG), 256, 0, st>>>(a.partials, *nblocks, p2);
+    const long long nb = adj_blocks(a);
+    double* p2 = base + (long long)ADJ_SLICES * nb * NG;
+    k_grad_sum2<<<dim3(GRAD_CHUNKS, NG), 256, 0, st>>>(base, nb, NG, nslice, p2);
     k_grad_sum3<<<1, 64, 0, st>>>(p2, NG, a.grad_acc);
     return cudaGetLastError();
 }
 
+template <class L, int UK>
+static cudaError_t adj_w(bool walls, const AdjArgs& a, cudaStream_t st, bool reduce)
+{
+    dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)((a.ny + a.rows - 1) / a.rows), (unsigned)a.nz);
+    if (walls) k_adjoint<L, UK, true><<<grid, 256, 0, st>>>(a);
+    else k_adjoint<L, UK, false><<<grid, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !reduce) return e;
+    return grad_reduce<L>(a, a.partials, 1, st);
+}
+
 template <class L>
-static cudaError_t adj_u(int uk, bool walls, const AdjArgs& a, cudaStream_t st, long long* nb)
+static cudaError_t adj_u(int uk, bool walls, const AdjArgs& a, cudaStream_t st, bool reduce)
 {
     switch (uk) {
-        case U_FIELD: return adj_w<L, U_FIELD>(walls, a, st, nb);
-        case U_ROW: return adj_w<L, U_ROW>(walls, a, st, nb);
-        default: return adj_w<L, U_NONE>(walls, a, st, nb);
+        case U_FIELD: return adj_w<L, U_FIELD>(walls, a, st, reduce);
+        case U_ROW: return adj_w<L, U_ROW>(walls, a, st, reduce);
+        default: return adj_w<L, U_NONE>(walls, a, st, reduce);
     }
 }
 
-cudaError_t launch_adjoint(int q, int ukind, bool walls, const AdjArgs& a, cudaStream_t st)
+cudaError_t launch_adjoint(int q, int ukind, bool walls, const AdjArgs& a, cudaStream_t st, bool reduce)
 {
-    long long nb = 0;
-    return q == 9 ? adj_u<D2Q9>(ukind, walls, a, st, &nb) : adj_u<D3Q15>(ukind, walls, a, st, &nb);
+    return q == 9 ? adj_u<D2Q9>(ukind, walls, a, st, reduce) : adj_u<D3Q15>(ukind, walls, a, st, reduce);
+}
+
+cudaError_t launch_grad_reduce(int q, const AdjArgs& a, double* base, int nslice, cudaStream_t st)
+{
+    return q == 9 ? grad_reduce<D2Q9>(a, base, nslice, st) : grad_reduce<D3Q15>(a, base, nslice, st);
+}
+
+long long adjoint_slice_size(int q, long long nx, long long ny, long long nz)
+{
+    const int rows = adjoint_rows(nx, ny, nz);
+    return ((nx + 255) / 256) * ((ny + rows - 1) / rows) * nz * (q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>());
 }
 
 long long adjoint_partials_size(int q, long long nx, long long ny, long long nz)
 {
-    const long long nb = ((nx + 255) / 256) * ((ny + ADJ_ROWS - 1) / ADJ_ROWS) * nz;
-    return (nb + GRAD_CHUNKS) * (q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>());
+    const int rows = adjoint_rows(nx, ny, nz);
+    const long long nb = ((nx + 255) / 256) * ((ny + rows - 1) / rows) * nz;
+    return (ADJ_SLICES * nb + GRAD_CHUNKS) * (q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>());
 }
 
 int adjoint_ngrad(int q) { return q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>(); }

@@ -713,6 +713,7 @@ static lbm::AdjArgs make_adj(lbm_cde_t h, int64_t k, const float* mu_in, float* 
     a.sched_len = h->sched_len;
     a.k = k;
     a.srow = lbm::sched_row(k, h->sched ? h->sched_len : 0);
+    a.rows = lbm::adjoint_rows(h->d.nx, h->d.ny, h->d.nz);
     a.nx = (int)h->d.nx;
     a.ny = (int)h->d.ny;
     a.nz = (int)h->d.nz;
@@ -739,7 +740,7 @@ lbm_status lbm_cde_adjoint_step(lbm_cde_t h, int64_t k, const float* mu_k_dev, f
     s = ensure_adjoint_buffers(h);
     if (s != LBM_OK) return s;
     lbm::AdjArgs a = make_adj(h, k, mu_k_dev, mu_prev_dev, f_prev_dev, dL_da_dev, grad_acc_dev);
-    CK(h, lbm::launch_adjoint(h->q, ukind_internal(h->ukind), h->d.bc_lo_y != LBM_BC_PERIODIC, a, h->st));
+    CK(h, lbm::launch_adjoint(h->q, ukind_internal(h->ukind), h->d.bc_lo_y != LBM_BC_PERIODIC, a, h->st, true));
     return LBM_OK;
 }
 
@@ -856,6 +857,8 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
     const int uk = ukind_internal(h->ukind);
     const bool walls = h->d.bc_lo_y != LBM_BC_PERIODIC;
     CK(h, cudaMemsetAsync(h->grad_acc, 0, sizeof(double) * ng, h->st));
+    const long long slice = lbm::adjoint_slice_size(h->q, h->d.nx, h->d.ny, h->d.nz);
+    int nslice = 0;   // reverse steps since the last gradient reduction
     if (dL_da_dev) CK(h, cudaMemsetAsync(dL_da_dev, 0, (size_t)h->ncell * 4 * h->dim, h->st));
     CK(h, lbm::launch_adjoint_seed(dL_dphiN_dev, h->mu[0], h->ncell, h->q, h->st));
     int cur = 0;
@@ -879,11 +882,17 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
         for (int64_t k = end; k > start; --k) {
             lbm::AdjArgs a = make_adj(h, k, h->mu[cur], h->mu[1 - cur], seg_state(j, k - 1 - start), dL_da_dev,
                                       h->grad_acc);
-            CK(h, lbm::launch_adjoint(h->q, uk, walls, a, h->st));
+            a.partials = h->adj_partials + nslice * slice;
+            CK(h, lbm::launch_adjoint(h->q, uk, walls, a, h->st, false));
+            if (++nslice == lbm::ADJ_SLICES) {
+                CK(h, lbm::launch_grad_reduce(h->q, a, h->adj_partials, nslice, h->st));
+                nslice = 0;
+            }
             cur ^= 1;
         }
     }
     lbm::AdjArgs a0 = make_adj(h, 0, h->mu[cur], nullptr, nullptr, dL_da_dev, h->grad_acc);
+    if (nslice > 0) CK(h, lbm::launch_grad_reduce(h->q, a0, h->adj_partials, nslice, h->st));
     CK(h, lbm::launch_adjoint_init(h->q, uk, a0, h->phi0_saved, dL_dphi0_dev, h->st));
     double g[33];
     CK(h, cudaMemcpyAsync(g, h->grad_acc, sizeof(double) * ng, cudaMemcpyDeviceToHost, h->st));

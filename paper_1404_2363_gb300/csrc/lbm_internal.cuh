@@ -84,6 +84,7 @@ struct AdjArgs {
     long long sched_len;
     long long k;          // the forward step being reversed (collision with u(k))
     int srow;             // k mod sched_len, or -1 without a schedule
+    int rows;             // grid rows per block (adjoint_rows)
     int nx, ny, nz;
     long long ncell;
     int bc_lo, bc_hi;
@@ -123,11 +124,19 @@ cudaError_t launch_phi(int q, int store, const StepArgs& a, float* phi_out, cuda
 cudaError_t launch_sum(int q, int store, const StepArgs& a, double* partials, int nblocks,
                        double* out_dev, cudaStream_t st);
 
-cudaError_t launch_adjoint(int q, int ukind, bool walls, const AdjArgs& a, cudaStream_t st);
+// reduce = true: also add the block partials to grad_acc (one step at a time);
+// a backward sweep writes the partials of up to ADJ_SLICES consecutive steps to
+// separate slices (AdjArgs::partials = base + slice * adjoint_slice_size) and
+// reduces them together with launch_grad_reduce.
+cudaError_t launch_adjoint(int q, int ukind, bool walls, const AdjArgs& a, cudaStream_t st, bool reduce);
+cudaError_t launch_grad_reduce(int q, const AdjArgs& a, double* base, int nslice, cudaStream_t st);
+long long adjoint_slice_size(int q, long long nx, long long ny, long long nz);
+constexpr int ADJ_SLICES = 16;   // reverse steps whose block partials are kept apart before one reduction
 cudaError_t launch_adjoint_init(int q, int ukind, const AdjArgs& a, const float* phi0, float* dphi0,
                                 cudaStream_t st);
 cudaError_t launch_adjoint_seed(const float* g, float* mu, long long ncell, int q, cudaStream_t st);
 long long adjoint_partials_size(int q, long long nx, long long ny, long long nz);
+int adjoint_rows(long long nx, long long ny, long long nz);
 int adjoint_ngrad(int q);
 
 }  // namespace lbm
