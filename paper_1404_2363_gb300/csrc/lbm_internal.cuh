@@ -110,6 +110,14 @@ inline void set_step(StepArgs& a, long long k)
     a.srow_prev = sched_row(k - 1, a.sched ? a.sched_len : 0);
 }
 
+// The node-quad D2Q9 kernel needs nx % 4 == 0, int offsets and a 16-byte
+// aligned velocity field (it reads four nodes per vector load).
+inline bool quad_ok(const StepArgs& a, int ukind)
+{
+    return a.nx % 4 == 0 && a.nz == 1 && 12LL * a.ncell < (1LL << 31) &&
+           (ukind != U_FIELD || (reinterpret_cast<uintptr_t>(a.ua) & 15) == 0);
+}
+
 struct LaunchCfg {
     int block;   // threads per block (multiple of 32)
     int vec;     // cells per thread along x (1, 2 or 4)

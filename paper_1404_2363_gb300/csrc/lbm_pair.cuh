@@ -141,16 +141,22 @@ __device__ __forceinline__ float2 collide_pair_f32(float2 (&v)[9], float2 ux, fl
 template <int S> struct Pair;
 template <> struct Pair<ST_F16> {
     using T2 = __half2;
+    static constexpr float scale = F16_SCALE;   // stored value = scale x offset
     __device__ static float2 to_f(__half2 h) { return mul2(__half22float2(h), sp2(1.0f / F16_SCALE)); }
     __device__ static __half2 from_f(float2 v) { return __float22half2_rn(mul2(v, sp2(F16_SCALE))); }
+    __device__ static float2 to_f_raw(__half2 h) { return __half22float2(h); }
+    __device__ static __half2 from_f_raw(float2 v) { return __float22half2_rn(v); }
     __device__ static __half2 join(__half2 lo_src, __half2 hi_src) {   // (lo_src.y, hi_src.x)
         return __halves2half2(__high2half(lo_src), __low2half(hi_src));
     }
 };
 template <> struct Pair<ST_BF16> {
     using T2 = __nv_bfloat162;
+    static constexpr float scale = 1.f;
     __device__ static float2 to_f(__nv_bfloat162 h) { return __bfloat1622float2(h); }
     __device__ static __nv_bfloat162 from_f(float2 v) { return __float22bfloat162_rn(v); }
+    __device__ static float2 to_f_raw(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+    __device__ static __nv_bfloat162 from_f_raw(float2 v) { return __float22bfloat162_rn(v); }
     __device__ static __nv_bfloat162 join(__nv_bfloat162 lo_src, __nv_bfloat162 hi_src) {
         return __halves2bfloat162(__high2bfloat16(lo_src), __low2bfloat16(hi_src));
     }
@@ -301,6 +307,245 @@ __global__ void __launch_bounds__(256) k_step_pair_d2q9(const StepArgs a)
 #pragma unroll
     for (int i = 0; i < 9; ++i) dst[i * NP + cellp] = P::from_f(f[i]);
     *reinterpret_cast<float2*>(a.phi_dst + 2 * cellp) = phi;
+}
+
+
+// ---------------------------------------------------------------------------
+// D2Q9 step on node quads: one thread owns x0 .. x0 + 3 (x0 = 4 t, nx % 4 == 0)
+// of one row and moves its data with 128-bit (FP32) or 64-bit (16-bit)
+// loads and stores. A pull shifted by one column needs one element of the
+// neighbouring quad: it comes from the adjacent lane by a warp shuffle, and
+// from memory only at warp edges and at the periodic seam. The decode is
+// scalar; the collisions run as two paired FP32 pairs (collide_pair /
+// collide_pair_f32). The FP16 form runs in units of 2^11 (the stored scale):
+// the decode weights are scaled by 2^11, so the pulled populations, the
+// collision and the new offsets all carry the factor exactly (a power of two)
+// and neither the loads nor the stores multiply; only phi is scaled back.
+// ---------------------------------------------------------------------------
+template <int STORE> struct Quad;
+template <> struct Quad<ST_F32> {
+    // quad of plane values at columns x0 .. x0 + 3
+    using W = float4;
+    __device__ static W load(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+};
+
+template <int STORE>
+struct QuadH {   // 16-bit: two 32-bit words (x0, x0 + 1), (x0 + 2, x0 + 3)
+    using T2 = typename Pair<STORE>::T2;
+    __device__ static uint2 load(const void* p) { return __ldg(reinterpret_cast<const uint2*>(p)); }
+    __device__ static T2 as_t2(unsigned w) { return *reinterpret_cast<const T2*>(&w); }
+    __device__ static unsigned as_u(T2 h) { return *reinterpret_cast<const unsigned*>(&h); }
+};
+
+// The six window values v(x0 - 1) .. v(x0 + 4) of one FP32 plane row around the quad.
+__device__ __forceinline__ void window6(const float* row, int x0c, int xl, int xr, bool needL, bool needR,
+                                        float (&w)[6])
+{
+    const float4 m = __ldg(reinterpret_cast<const float4*>(row + x0c));
+    float l = __shfl_up_sync(0xffffffffu, m.w, 1);
+    float r = __shfl_down_sync(0xffffffffu, m.x, 1);
+    if (needL) l = __ldg(row + xl);
+    if (needR) r = __ldg(row + xr);
+    w[0] = l;
+    w[1] = m.x;
+    w[2] = m.y;
+    w[3] = m.z;
+    w[4] = m.w;
+    w[5] = r;
+}
+
+template <int STORE, int UK, bool WALLS>
+__global__ void __launch_bounds__(256, 4) k_step_quad_d2q9(const StepArgs a)
+{
+    using L = D2Q9;
+    constexpr bool NEQ = STORE != ST_F32;
+    constexpr float SC = STORE == ST_F16 ? F16_SCALE : 1.f;   // working units (see above)
+    const int nx = a.nx, ny = a.ny;
+    const int N = (int)a.ncell;
+    const int y = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int x0 = 4 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const bool live = x0 < nx;
+    const int x0c = live ? x0 : nx - 4;             // dead lanes still take part in the shuffles
+    const int xl = x0c == 0 ? nx - 1 : x0c - 1;     // column x0 - 1
+    const int xr = x0c + 4 == nx ? 0 : x0c + 4;     // column x0 + 4
+    const bool needL = lane == 0 || x0c == 0;
+    const bool needR = lane == 31 || x0c + 4 >= nx;
+    const int ys[3] = {y + 1 == ny ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};   // source row by e_y + 1
+    const Coef& c = a.c;
+    Coef cd = a.c;    // decode weights in working units
+    if (SC != 1.f) {
+        cd.w0 *= SC;
+        cd.wa *= SC;
+        cd.wd *= SC;
+        cd.ka *= SC;
+        cd.kd *= SC;
+    }
+    float s_now[3], s_prev[3];
+    sched_row_at(a.sched, a.srow_now, 2, s_now);
+    sched_row_at(a.sched, a.srow_prev, 2, s_prev);
+
+    float f[9][4];    // pulled (and decoded) populations of the four nodes, working units
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int row = ys[r] * nx;
+        float P[6], Ux[6], Uy[6];
+        if (NEQ) {
+            window6(a.phi_src + row, x0c, xl, xr, needL, needR, P);
+            if (UK == U_FIELD) {
+                window6(a.ua + row, x0c, xl, xr, needL, needR, Ux);
+                window6(a.ua + N + row, x0c, xl, xr, needL, needR, Uy);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    Ux[k] = __fmul_rn(Ux[k], s_prev[0]);
+                    Uy[k] = __fmul_rn(Uy[k], s_prev[1]);
+                }
+            } else {
+                float ux = 0.f, uy = 0.f;
+                if (UK == U_ROW) {
+                    ux = __fmul_rn(__ldg(a.ua + ys[r]), s_prev[0]);
+                    uy = __fmul_rn(__ldg(a.ua + a.ny + ys[r]), s_prev[1]);
+                }
+#pragma unroll
+                for (int k = 0; k < 6; ++k) Ux[k] = ux, Uy[k] = uy;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (L::ey(i) + 1 != r) continue;
+            const int ex = L::ex(i);
+            float g[4];
+            if constexpr (!NEQ) {
+                float w[6];
+                const float* prow = static_cast<const float*>(a.src) + i * N + row;
+                if (ex == 0) {
+                    const float4 m = __ldg(reinterpret_cast<const float4*>(prow + x0c));
+                    g[0] = m.x, g[1] = m.y, g[2] = m.z, g[3] = m.w;
+                } else {
+                    window6(prow, x0c, xl, xr, needL && ex > 0, needR && ex < 0, w);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) g[j] = w[j + 1 - ex];
+                }
+            } else {
+                using Q = QuadH<STORE>;
+                using P2 = Pair<STORE>;
+                const unsigned short* prow = static_cast<const unsigned short*>(a.src) + i * N + row;
+                const uint2 m = Q::load(prow + x0c);
+                unsigned w0 = m.x, w1 = m.y;
+                if (ex > 0) {            // columns x0 - 1 .. x0 + 2
+                    unsigned lw = __shfl_up_sync(0xffffffffu, m.y, 1);
+                    if (needL) lw = __ldg(reinterpret_cast<const unsigned*>(prow + (x0c == 0 ? nx - 2 : x0c - 2)));
+                    w0 = Q::as_u(P2::join(Q::as_t2(lw), Q::as_t2(m.x)));
+                    w1 = Q::as_u(P2::join(Q::as_t2(m.x), Q::as_t2(m.y)));
+                } else if (ex < 0) {     // columns x0 + 1 .. x0 + 4
+                    unsigned rw = __shfl_down_sync(0xffffffffu, m.x, 1);
+                    if (needR) rw = __ldg(reinterpret_cast<const unsigned*>(prow + xr));
+                    w0 = Q::as_u(P2::join(Q::as_t2(m.x), Q::as_t2(m.y)));
+                    w1 = Q::as_u(P2::join(Q::as_t2(m.y), Q::as_t2(rw)));
+                }
+                const float2 g01 = P2::to_f_raw(Q::as_t2(w0)), g23 = P2::to_f_raw(Q::as_t2(w1));
+                g[0] = g01.x, g[1] = g01.y, g[2] = g23.x, g[3] = g23.y;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float v = g[j];
+                if (NEQ) {
+                    const int sidx = j + 1 - ex;     // source column x0 + j - e_x in the window
+                    v = fmaf(P[sidx], feq_unit<L>(cd, i, Ux[sidx], Uy[sidx], 0.f), v);
+                }
+                f[i][j] = v;
+            }
+        }
+    }
+
+    // own raw velocity factors (for u(k) and the walls)
+    float axo[4] = {0.f, 0.f, 0.f, 0.f}, ayo[4] = {0.f, 0.f, 0.f, 0.f};
+    if (UK == U_FIELD) {
+        const float4 ax = __ldg(reinterpret_cast<const float4*>(a.ua + y * nx + x0c));
+        const float4 ay = __ldg(reinterpret_cast<const float4*>(a.ua + N + y * nx + x0c));
+        axo[0] = ax.x, axo[1] = ax.y, axo[2] = ax.z, axo[3] = ax.w;
+        ayo[0] = ay.x, ayo[1] = ay.y, ayo[2] = ay.z, ayo[3] = ay.w;
+    } else if (UK == U_ROW) {
+        const float ax = __ldg(a.ua + y), ay = __ldg(a.ua + a.ny + y);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) axo[j] = ax, ayo[j] = ay;
+    }
+    const int cell = y * nx + x0c;
+    if (WALLS) {
+        const bool lo = (y == 0) && a.bc_lo != BC_PERIODIC;
+        const bool hi = (y == ny - 1) && a.bc_hi != BC_PERIODIC;
+        if (lo || hi) {
+            const int kind = lo ? a.bc_lo : a.bc_hi;
+            const int inward = lo ? 1 : -1;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float ux = UK == U_NONE ? 0.f : __fmul_rn(axo[j], s_prev[0]);
+                const float uy = UK == U_NONE ? 0.f : __fmul_rn(ayo[j], s_prev[1]);
+                if (kind == BC_NOFLUX) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i)
+                        if (L::ey(i) == inward) f[i][j] = f[mirror_y<L>(i)][j];
+                } else if (kind == BC_BOUNCE) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i)
+                        if (L::ey(i) == inward) {
+                            const int o = opposite<L>(i);
+                            using T = typename StT<STORE>::T;
+                            float v = ldg_f(static_cast<const T*>(a.src) + o * N + cell + j) * SC;   // exact
+                            if (NEQ) v = fmaf(__ldg(a.phi_src + cell + j), feq_unit<L>(cd, o, ux, uy, 0.f), v);
+                            f[i][j] = v;
+                        }
+                } else {   // Dirichlet
+                    float known = 0.f, wk = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        if (L::ey(i) == inward) wk += feq_unit<L>(cd, i, ux, uy, 0.f);
+                        else known += f[i][j];
+                    }
+                    const float ps = ((lo ? a.phiw_lo : a.phiw_hi) * SC - known) / wk;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i)
+                        if (L::ey(i) == inward) f[i][j] = __fmul_rn(ps, feq_unit<L>(cd, i, ux, uy, 0.f));
+                }
+            }
+        }
+    }
+    // collisions of the pairs (x0, x0 + 1) and (x0 + 2, x0 + 3)
+    float2 out[2][9], phi[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float2 v[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v[i] = make_float2(f[i][2 * h], f[i][2 * h + 1]);
+        float2 ux = sp2(0.f), uy = sp2(0.f);
+        if (UK != U_NONE) {
+            ux = make_float2(__fmul_rn(axo[2 * h], s_now[0]), __fmul_rn(axo[2 * h + 1], s_now[0]));
+            uy = make_float2(__fmul_rn(ayo[2 * h], s_now[1]), __fmul_rn(ayo[2 * h + 1], s_now[1]));
+        }
+        if constexpr (NEQ) phi[h] = collide_pair(v, ux, uy, c);
+        else phi[h] = collide_pair_f32(v, ux, uy, c);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) out[h][i] = v[i];
+    }
+    if (!live) return;
+    if constexpr (NEQ) {
+        using P2 = Pair<STORE>;
+        using Q = QuadH<STORE>;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            uint2 w;
+            w.x = Q::as_u(P2::from_f_raw(out[0][i]));
+            w.y = Q::as_u(P2::from_f_raw(out[1][i]));
+            *reinterpret_cast<uint2*>(static_cast<unsigned short*>(a.dst) + i * N + cell) = w;
+        }
+        const float2 p0 = mul2(phi[0], sp2(1.f / SC)), p1 = mul2(phi[1], sp2(1.f / SC));
+        *reinterpret_cast<float4*>(a.phi_dst + cell) = make_float4(p0.x, p0.y, p1.x, p1.y);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            *reinterpret_cast<float4*>(static_cast<float*>(a.dst) + i * N + cell) =
+                make_float4(out[0][i].x, out[0][i].y, out[1][i].x, out[1][i].y);
+    }
 }
 
 }  // namespace lbm

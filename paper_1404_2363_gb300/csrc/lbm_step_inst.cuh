@@ -9,6 +9,15 @@ namespace lbm {
 template <class L, int STORE, int UK, bool WALLS>
 static cudaError_t step_vec(LaunchCfg cfg, const StepArgs& a, cudaStream_t st)
 {
+    if constexpr (L::Q == 9) {
+        if (cfg.vec == 6 && quad_ok(a, UK)) {
+            // node-quad variant: 128-bit / 64-bit vector loads and stores, four nodes per thread
+            const int per = 4 * cfg.block;
+            dim3 grid((unsigned)((a.nx + per - 1) / per), (unsigned)a.ny, 1);
+            k_step_quad_d2q9<STORE, UK, WALLS><<<grid, cfg.block, 0, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (L::Q == 9 && STORE != ST_F32) {
         if (cfg.vec == 5 && a.nx % 2 == 0 && a.nz == 1 && 12LL * a.ncell < (1LL << 31)) {
             // node-pair variant (paired FP32 arithmetic, two adjacent nodes per thread)

@@ -153,6 +153,37 @@ def test_pair_offset_kernel(O, storage, bc, ukind):
         assert np.array_equal(got, one)
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("bc,ukind", [(("periodic", "periodic"), "field"), (("noflux", "noflux"), "row"),
+                                      (("bounceback", "bounceback"), "field"),
+                                      (("dirichlet", "dirichlet"), "field"), (("periodic", "periodic"), "none")])
+def test_quad_kernel(O, storage, bc, ukind):
+    """The node-quad kernel (launch vec = 6: four nodes per thread, 128-bit FP32 /
+    64-bit 16-bit vector loads and stores, warp shuffles for the shifted pulls)
+    against the oracle on a 300 x 37 grid (75 quads per row: ragged 64-thread
+    blocks and a partial warp at the seam), and against the one-node kernel."""
+    case = Case(storage=storage, bc=bc, ukind=ukind, sched=ukind != "none", nx=300, ny=37,
+                phi_w=(1.0, 0.25) if bc[0] == "dirichlet" else (0.0, 0.0))
+    phi0, a, sched = case.inputs()
+    got, _ = _run_vec3(case, phi0, a, sched, vec=6, block=64)
+    want = run_oracle(O, case, phi0, a, sched)
+    assert rel_l2(got, want) <= TOL[storage]
+    one, _ = _run_vec3(case, phi0, a, sched, vec=1, block=64)
+    assert rel_l2(got, one) <= TOL[storage] / 4
+
+
+@pytest.mark.parametrize("nx,ny", [(4, 6), (8, 5), (132, 9)])
+def test_quad_kernel_narrow_grids(O, nx, ny):
+    """One quad per row (both shuffle partners are fix-up loads across the
+    periodic seam), two quads, and 33 quads (a warp edge inside the row)."""
+    for storage in ("f32", "bf16"):
+        case = Case(storage=storage, nx=nx, ny=ny, steps=40)
+        phi0, a, sched = case.inputs()
+        got, _ = _run_vec3(case, phi0, a, sched, vec=6, block=32)
+        want = run_oracle(O, case, phi0, a, sched)
+        assert rel_l2(got, want) <= TOL[storage], (storage, nx, ny)
+
+
 def _run_vec3(case, phi0, a, sched, vec=3, block=256):
     import torch
     from paper_1404_2363_gb300.solver import Solver
