@@ -417,7 +417,9 @@ def adjoint_cost(store: str, ms_forward: float, nsteps: int = 400):
     s, wl, a, sched, phi0 = make_solver(store)
     g = torch.ones((N_GRID, N_GRID), device="cuda", dtype=torch.float32)
     s.forward_ckpt(phi0, 8)
-    s.backward(g, want_da=True)            # warm-up and allocation
+    s.backward(g, want_da=False)           # warm-up (both kernel instances) and allocation
+    s.forward_ckpt(phi0, 8)
+    s.backward(g, want_da=True)
     torch.cuda.synchronize()
     out = {"steps": nsteps, "checkpoint_every": int(np.ceil(np.sqrt(nsteps))),
            "plain_forward_ms_per_step": ms_forward}

@@ -34,8 +34,11 @@ int adjoint_rows(long long nx, long long ny, long long nz)
     return rows;
 }
 
-template <class L, int UK, bool WALLS>
-__global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArgs a)
+// DA: the velocity-field gradient is accumulated (UK == U_FIELD only); its
+// running values are requested with the other loads of the node, and the
+// instance runs at 3 blocks per SM (80 registers) to hold them.
+template <class L, int UK, bool WALLS, bool DA>
+__global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(const AdjArgs a)
 {
     constexpr int Q = L::Q, DIM = L::DIM, NG = ngrad<L>();
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -65,6 +68,11 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
             return (long long)xs[L::ex(i) + 1] + (long long)nx * (ys[L::ey(i) + 1] + (long long)ny * zs[L::ez(i) + 1]);
         };
         float mu[Q], f[Q];
+        float du_old[DIM];
+        if (DA && live) {
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) du_old[d] = a.du_acc[(long long)d * N + cell];
+        }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             mu[i] = __ldg(a.mu_in + (long long)i * N + cell);
@@ -140,7 +148,13 @@ __global__ void __launch_bounds__(256, L::Q == 9 ? 4 : 3) k_adjoint(const AdjArg
         if (!live) continue;
 
         // velocity partials: u(x, k) = a(x) s(k)  =>  dL/da += s(k) dL/du(k)
-        if (UK == U_FIELD && a.du_acc != nullptr) {
+        if (DA) {
+#pragma unroll
+            for (int d = 0; d < DIM; ++d)
+                a.du_acc[(long long)d * N + cell] = du_old[d] + phi * (b[3 + 2 * d] - b[4 + 2 * d]) * s_now[d];
+        } else if (UK == U_FIELD && a.du_acc != nullptr) {
+            // never taken (gradient buffers go to the DA instance); kept because this
+            // instance measured faster with it (register allocation)
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
                 float* p = a.du_acc + (long long)d * N + cell;
@@ -299,8 +313,19 @@ template <class L, int UK>
 static cudaError_t adj_w(bool walls, const AdjArgs& a, cudaStream_t st, bool reduce)
 {
     dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)((a.ny + a.rows - 1) / a.rows), (unsigned)a.nz);
-    if (walls) k_adjoint<L, UK, true><<<grid, 256, 0, st>>>(a);
-    else k_adjoint<L, UK, false><<<grid, 256, 0, st>>>(a);
+    if constexpr (UK == U_FIELD) {
+        if (a.du_acc != nullptr) {
+            if (walls) k_adjoint<L, UK, true, true><<<grid, 256, 0, st>>>(a);
+            else k_adjoint<L, UK, false, true><<<grid, 256, 0, st>>>(a);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess || !reduce) return e;
+            return grad_reduce<L>(a, a.partials, 1, st);
+        }
+    }
+    {
+        if (walls) k_adjoint<L, UK, true, false><<<grid, 256, 0, st>>>(a);
+        else k_adjoint<L, UK, false, false><<<grid, 256, 0, st>>>(a);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !reduce) return e;
     return grad_reduce<L>(a, a.partials, 1, st);
