@@ -226,7 +226,7 @@ lbm_status lbm_cde_run_host(lbm_cde_t h, const float* phi0_host, int64_t nsteps,
  * mu_{k-1} = P^T C_k^T mu_k. Supported: FP32 storage, periodic / NOFLUX_NODE /
  * BOUNCEBACK walls (LBM_E_UNSUPPORTED otherwise). */
 
-/* Number of FP64 gradient accumulators of one reverse step: 2 dim^2 + q
+/* Number of gradient accumulators of one reverse step: 2 dim^2 + q
  * (G_A[dim][dim], G_AC[dim][dim], G_diag[q]; see lbm_cde_grad_rates). */
 int32_t lbm_cde_adjoint_ngrad(int32_t lattice);
 
@@ -234,7 +234,11 @@ int32_t lbm_cde_adjoint_ngrad(int32_t lattice);
  *   mu_k_dev    : dL/dB_k, device FP32 [q][ncell]
  *   mu_prev_dev : receives dL/dB_{k-1} (must not alias mu_k_dev)
  *   f_prev_dev  : the forward state B_{k-1}, device FP32 [q][ncell]
- *   grad_acc_dev: device FP64 [lbm_cde_adjoint_ngrad]; the partials
+ *   grad_acc_dev: device FP32 [2 x lbm_cde_adjoint_ngrad], 8-byte aligned,
+ *                 caller-owned, zeroed by the caller before the first step:
+ *                 compensated sums, accumulator j = grad_acc_dev[2j] +
+ *                 grad_acc_dev[2j + 1] (add them in FP64 on the host before
+ *                 lbm_cde_grad_rates; the GPU does no FP64 arithmetic); the partials
  *                 G_A[a][b] += -sum (M^-T mu)_{j_a} (m - m^eq)_{j_b},
  *                 G_AC[a][b] += -sum (M^-T mu)_{j_a} (m - m^eq)_{q_b},
  *                 G_diag[r] += -sum (M^-T mu)_r (m - m^eq)_r are added
@@ -243,7 +247,7 @@ int32_t lbm_cde_adjoint_ngrad(int32_t lattice);
  *                 LBM_U_FIELD velocity u = a(x) s(t)
  * Asynchronous. Errors: LBM_E_ARG, LBM_E_UNSUPPORTED, LBM_E_STATE, LBM_E_OOM. */
 lbm_status lbm_cde_adjoint_step(lbm_cde_t h, int64_t k, const float* mu_k_dev, float* mu_prev_dev,
-                                const float* f_prev_dev, double* grad_acc_dev, float* dL_da_dev);
+                                const float* f_prev_dev, float* grad_acc_dev, float* dL_da_dev);
 
 /* Converts accumulated partials g (host, lbm_cde_adjoint_ngrad doubles) into
  * dL/dD (host, dim x dim, every entry an independent variable; includes the

@@ -12,14 +12,40 @@
 // pre-collision state f_k = P B_{k-1} is pulled again to form the parameter
 // partials  dL/dS_rc = -sum a_r (m - m^eq)_c  and the velocity partials
 //     dL/du_a = phi (b_{j_a} - b_{q_a})   (j_a, q_a: flux and energy-flux rows).
-// Gradient partials are summed per warp in FP32, per block and over blocks in
-// FP64, in a fixed order.
+// Gradient partials are summed in FP32 per thread, warp and block, and over
+// blocks and steps as compensated FP32 sums (error-free TwoSum: value = sum +
+// compensation), in a fixed order; no FP64 arithmetic runs on the GPU here.
 #include "lbm_device.cuh"
 
 namespace lbm {
 
 template <class L>
 __host__ __device__ constexpr int ngrad() { return 2 * L::DIM * L::DIM + L::Q; }
+
+// Error-free transformation of a + b (TwoSum, Knuth): returns fl(a + b) and
+// sets e so that a + b = s + e exactly. Explicit roundings: never reassociated.
+__device__ __forceinline__ float two_sum(float a, float b, float& e)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+// compensated sums (x: sum, y: accumulated rounding errors)
+__device__ __forceinline__ void csum_add(float2& acc, float v)
+{
+    float e;
+    acc.x = two_sum(acc.x, v, e);
+    acc.y = __fadd_rn(acc.y, e);
+}
+
+__device__ __forceinline__ void csum_merge(float2& acc, float2 o)
+{
+    float e;
+    acc.x = two_sum(acc.x, o.x, e);
+    acc.y = __fadd_rn(__fadd_rn(acc.y, o.y), e);
+}
 
 // Rows handled by one block of the adjoint kernel (AdjArgs::rows): the gradient
 // partials of that many nodes per thread are summed in registers before the
@@ -194,8 +220,7 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(con
         }
     }
 
-    // block reduction of the gradient partials: FP32 within a warp (FP64
-    // throughput is a small fraction of FP32 on this GPU), FP64 beyond
+    // block reduction of the gradient partials (FP32)
 #pragma unroll
     for (int j = 0; j < NG; ++j)
         for (int off = 16; off > 0; off >>= 1) g[j] += __shfl_down_sync(0xffffffffu, g[j], off);
@@ -206,9 +231,9 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(con
         for (int j = 0; j < NG; ++j) red[warp][j] = g[j];
     __syncthreads();
     if ((int)threadIdx.x < NG) {
-        double s = 0.0;
+        float s = 0.f;
         const int nw = (blockDim.x + 31) >> 5;
-        for (int w = 0; w < nw; ++w) s += (double)red[w][threadIdx.x];
+        for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
         const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
         const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
         a.partials[threadIdx.x * nb + blk] = s;   // [NG][nblocks]: coalesced in the reduction
@@ -221,35 +246,35 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(con
 // adds the chunk sums in index order to the running totals.
 constexpr int GRAD_CHUNKS = 32;
 
-__global__ void __launch_bounds__(256) k_grad_sum2(const double* __restrict__ partials, long long nblocks,
-                                                   int ng, int nslice, double* __restrict__ p2)
+__global__ void __launch_bounds__(256) k_grad_sum2(const float* __restrict__ partials, long long nblocks,
+                                                   int ng, int nslice, float2* __restrict__ p2)
 {
     const int r = blockIdx.x, j = blockIdx.y;
     const long long len = (nblocks + GRAD_CHUNKS - 1) / GRAD_CHUNKS;
     const long long b0 = r * len;
     const long long b1 = b0 + len < nblocks ? b0 + len : nblocks;
-    double s = 0.0;
+    float2 s = make_float2(0.f, 0.f);
     for (int sl = 0; sl < nslice; ++sl) {
-        const double* row = partials + ((long long)sl * ng + j) * nblocks;
-        for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) s += row[b];
+        const float* row = partials + ((long long)sl * ng + j) * nblocks;
+        for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) csum_add(s, row[b]);
     }
-    __shared__ double red[256];
+    __shared__ float2 red[256];
     red[threadIdx.x] = s;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        if ((int)threadIdx.x < w) csum_merge(red[threadIdx.x], red[threadIdx.x + w]);
         __syncthreads();
     }
     if (threadIdx.x == 0) p2[(long long)j * GRAD_CHUNKS + r] = red[0];
 }
 
-__global__ void k_grad_sum3(const double* __restrict__ p2, int ng, double* __restrict__ acc)
+__global__ void k_grad_sum3(const float2* __restrict__ p2, int ng, float2* __restrict__ acc)
 {
     const int j = threadIdx.x;
     if (j >= ng) return;
-    double s = 0.0;
-    for (int r = 0; r < GRAD_CHUNKS; ++r) s += p2[j * GRAD_CHUNKS + r];
-    acc[j] += s;
+    float2 s = acc[j];
+    for (int r = 0; r < GRAD_CHUNKS; ++r) csum_merge(s, p2[j * GRAD_CHUNKS + r]);
+    acc[j] = s;
 }
 
 // Gradients through the initial state B_0 = f^eq(phi0, u(0)):
@@ -299,11 +324,12 @@ static long long adj_blocks(const AdjArgs& a)
 
 // grad_acc += the per-block partials of nslice slices starting at base, summed in a fixed order
 template <class L>
-static cudaError_t grad_reduce(const AdjArgs& a, double* base, int nslice, cudaStream_t st)
+static cudaError_t grad_reduce(const AdjArgs& a, float* base, int nslice, cudaStream_t st)
 {
     constexpr int NG = ngrad<L>();
     const long long nb = adj_blocks(a);
-    double* p2 = base + (long long)ADJ_SLICES * nb * NG;
+    const long long off = ((long long)ADJ_SLICES * nb * NG + 1) & ~1LL;   // 8-byte aligned chunk sums
+    float2* p2 = reinterpret_cast<float2*>(base + off);
     k_grad_sum2<<<dim3(GRAD_CHUNKS, NG), 256, 0, st>>>(base, nb, NG, nslice, p2);
     k_grad_sum3<<<1, 64, 0, st>>>(p2, NG, a.grad_acc);
     return cudaGetLastError();
@@ -346,7 +372,7 @@ cudaError_t launch_adjoint(int q, int ukind, bool walls, const AdjArgs& a, cudaS
     return q == 9 ? adj_u<D2Q9>(ukind, walls, a, st, reduce) : adj_u<D3Q15>(ukind, walls, a, st, reduce);
 }
 
-cudaError_t launch_grad_reduce(int q, const AdjArgs& a, double* base, int nslice, cudaStream_t st)
+cudaError_t launch_grad_reduce(int q, const AdjArgs& a, float* base, int nslice, cudaStream_t st)
 {
     return q == 9 ? grad_reduce<D2Q9>(a, base, nslice, st) : grad_reduce<D3Q15>(a, base, nslice, st);
 }
@@ -361,7 +387,8 @@ long long adjoint_partials_size(int q, long long nx, long long ny, long long nz)
 {
     const int rows = adjoint_rows(nx, ny, nz);
     const long long nb = ((nx + 255) / 256) * ((ny + rows - 1) / rows) * nz;
-    return (ADJ_SLICES * nb + GRAD_CHUNKS) * (q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>());
+    // ADJ_SLICES slices of [NG][nb] floats, then the [NG][GRAD_CHUNKS] float2 chunk sums
+    return (ADJ_SLICES * nb + 2 * GRAD_CHUNKS) * (q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>()) + 2;
 }
 
 int adjoint_ngrad(int q) { return q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>(); }

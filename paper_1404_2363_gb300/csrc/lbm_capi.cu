@@ -49,8 +49,8 @@ struct lbm_cde_s {
     void* seg = nullptr;
     int64_t seg_states = 0;
     float* mu[2] = {nullptr, nullptr};
-    double* adj_partials = nullptr;
-    double* grad_acc = nullptr;
+    float* adj_partials = nullptr;
+    float2* grad_acc = nullptr;
     float* phi0_saved = nullptr;
     bool have_fwd = false;
 };
@@ -698,15 +698,15 @@ static lbm_status ensure_adjoint_buffers(lbm_cde_t h)
     if (!h->adj_partials) {
         const long long np = lbm::adjoint_partials_size(h->q, h->d.nx, h->d.ny, h->d.nz);
         const int ng = lbm::adjoint_ngrad(h->q);
-        h->adj_partials = static_cast<double*>(dev_alloc(h, sizeof(double) * (np + ng)));
+        h->adj_partials = static_cast<float*>(dev_alloc(h, sizeof(float) * (np + 2 * ng)));
         if (!h->adj_partials) return fail(h, LBM_E_OOM, "adjoint scratch allocation failed");
-        h->grad_acc = h->adj_partials + np;
+        h->grad_acc = reinterpret_cast<float2*>(h->adj_partials + np);   // np is even
     }
     return LBM_OK;
 }
 
 static lbm::AdjArgs make_adj(lbm_cde_t h, int64_t k, const float* mu_in, float* mu_out, const float* fprev,
-                             float* du, double* grad_acc)
+                             float* du, float2* grad_acc)
 {
     lbm::AdjArgs a{};
     a.mu_in = mu_in;
@@ -732,7 +732,7 @@ static lbm::AdjArgs make_adj(lbm_cde_t h, int64_t k, const float* mu_in, float* 
 }
 
 lbm_status lbm_cde_adjoint_step(lbm_cde_t h, int64_t k, const float* mu_k_dev, float* mu_prev_dev,
-                                const float* f_prev_dev, double* grad_acc_dev, float* dL_da_dev)
+                                const float* f_prev_dev, float* grad_acc_dev, float* dL_da_dev)
 {
     if (!h || !mu_k_dev || !mu_prev_dev || !f_prev_dev || !grad_acc_dev || k < 1)
         return fail(h, LBM_E_ARG, "bad argument");
@@ -743,7 +743,9 @@ lbm_status lbm_cde_adjoint_step(lbm_cde_t h, int64_t k, const float* mu_k_dev, f
         return fail(h, LBM_E_UNSUPPORTED, "velocity gradients need a velocity field (LBM_U_FIELD)");
     s = ensure_adjoint_buffers(h);
     if (s != LBM_OK) return s;
-    lbm::AdjArgs a = make_adj(h, k, mu_k_dev, mu_prev_dev, f_prev_dev, dL_da_dev, grad_acc_dev);
+    if (reinterpret_cast<uintptr_t>(grad_acc_dev) % 8 != 0) return fail(h, LBM_E_ARG, "grad_acc_dev not 8-byte aligned");
+    lbm::AdjArgs a = make_adj(h, k, mu_k_dev, mu_prev_dev, f_prev_dev, dL_da_dev,
+                              reinterpret_cast<float2*>(grad_acc_dev));
     CK(h, lbm::launch_adjoint(h->q, ukind_internal(h->ukind), h->d.bc_lo_y != LBM_BC_PERIODIC, a, h->st, true));
     return LBM_OK;
 }
@@ -860,7 +862,7 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
     const size_t sb = (size_t)h->ncell * 4 * h->q;
     const int uk = ukind_internal(h->ukind);
     const bool walls = h->d.bc_lo_y != LBM_BC_PERIODIC;
-    CK(h, cudaMemsetAsync(h->grad_acc, 0, sizeof(double) * ng, h->st));
+    CK(h, cudaMemsetAsync(h->grad_acc, 0, sizeof(float2) * ng, h->st));
     const long long slice = lbm::adjoint_slice_size(h->q, h->d.nx, h->d.ny, h->d.nz);
     int nslice = 0;   // reverse steps since the last gradient reduction
     if (dL_da_dev) CK(h, cudaMemsetAsync(dL_da_dev, 0, (size_t)h->ncell * 4 * h->dim, h->st));
@@ -898,9 +900,11 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
     lbm::AdjArgs a0 = make_adj(h, 0, h->mu[cur], nullptr, nullptr, dL_da_dev, h->grad_acc);
     if (nslice > 0) CK(h, lbm::launch_grad_reduce(h->q, a0, h->adj_partials, nslice, h->st));
     CK(h, lbm::launch_adjoint_init(h->q, uk, a0, h->phi0_saved, dL_dphi0_dev, h->st));
-    double g[33];
-    CK(h, cudaMemcpyAsync(g, h->grad_acc, sizeof(double) * ng, cudaMemcpyDeviceToHost, h->st));
+    float2 gc[33];
+    CK(h, cudaMemcpyAsync(gc, h->grad_acc, sizeof(float2) * ng, cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaStreamSynchronize(h->st));
+    double g[33];
+    for (int j = 0; j < ng; ++j) g[j] = (double)gc[j].x + (double)gc[j].y;   // compensated sum, host FP64
     return lbm_cde_grad_rates(h, g, dL_dD_host, dL_ds_host);
 }
 

@@ -90,8 +90,9 @@ struct AdjArgs {
     int bc_lo, bc_hi;
     Coef c;
     float* du_acc;        // dL/da accumulator [dim][ncell] (FIELD velocity) or nullptr
-    double* partials;     // per-block gradient partials [nblocks][ngrad]
-    double* grad_acc;     // [ngrad] running sums: G_A[dim][dim], G_AC[dim][dim], G_diag[q]
+    float* partials;      // per-block gradient partials [ngrad][nblocks] (one slice per step)
+    float2* grad_acc;     // [ngrad] running compensated sums (value = x + y): G_A[dim][dim],
+                          // G_AC[dim][dim], G_diag[q]
 };
 
 // Row of a schedule of length len for step k (k mod len), -1 without one;
@@ -137,13 +138,13 @@ cudaError_t launch_sum(int q, int store, const StepArgs& a, double* partials, in
 // separate slices (AdjArgs::partials = base + slice * adjoint_slice_size) and
 // reduces them together with launch_grad_reduce.
 cudaError_t launch_adjoint(int q, int ukind, bool walls, const AdjArgs& a, cudaStream_t st, bool reduce);
-cudaError_t launch_grad_reduce(int q, const AdjArgs& a, double* base, int nslice, cudaStream_t st);
+cudaError_t launch_grad_reduce(int q, const AdjArgs& a, float* base, int nslice, cudaStream_t st);
 long long adjoint_slice_size(int q, long long nx, long long ny, long long nz);
 constexpr int ADJ_SLICES = 16;   // reverse steps whose block partials are kept apart before one reduction
 cudaError_t launch_adjoint_init(int q, int ukind, const AdjArgs& a, const float* phi0, float* dphi0,
                                 cudaStream_t st);
 cudaError_t launch_adjoint_seed(const float* g, float* mu, long long ncell, int q, cudaStream_t st);
-long long adjoint_partials_size(int q, long long nx, long long ny, long long nz);
+long long adjoint_partials_size(int q, long long nx, long long ny, long long nz);   // in floats
 int adjoint_rows(long long nx, long long ny, long long nz);
 int adjoint_ngrad(int q);
 

@@ -216,3 +216,58 @@ def test_d3q15_adjoint_matches_oracle_and_fd(O):
         fd = (vals[0] - vals[1]) / (2 * h)
         an = dD[i, j] + (dD[j, i] if i != j else 0.0)
         assert abs(an - fd) <= 1e-4 * abs(fd) + 1e-7, (i, j, an, fd)
+
+
+def test_single_step_api_matches_backward():
+    """lbm_cde_adjoint_step driven step by step from the host (forward states kept
+    with get_state, compensated FP32 gradient accumulators) gives the same dL/dD
+    and dL/da as lbm_cde_backward."""
+    import ctypes
+
+    from paper_1404_2363_gb300 import _native as N
+
+    case = Case(nx=48, ny=36, steps=25)
+    phi0, a, sched = case.inputs()
+    g = np.random.default_rng(11).standard_normal(case.shape).astype(np.float32)
+    s = Solver(nx=case.nx, ny=case.ny)
+    s.set_D(case.D)
+    s.set_velocity(torch.from_numpy(a).cuda(), torch.from_numpy(sched).cuda())
+    # reference: the checkpointed reverse sweep
+    s.forward_ckpt(torch.from_numpy(phi0).cuda(), case.steps)
+    _, dD_ref, _, da_ref = s.backward(torch.from_numpy(g).cuda(), want_da=True)
+    # the same by single steps
+    s.set_phi(torch.from_numpy(phi0).cuda())
+    states = [s.get_state()[0].clone()]
+    for _ in range(case.steps):
+        s.step(1)
+        states.append(s.get_state()[0].clone())
+    q, n = 9, case.nx * case.ny
+    mu = torch.from_numpy(np.tile(g.reshape(1, -1), (q, 1))).cuda().contiguous()
+    mu_prev = torch.empty_like(mu)
+    ng = s.L.lbm_cde_adjoint_ngrad(N.LBM_D2Q9)
+    acc = torch.zeros(2 * ng, device="cuda", dtype=torch.float32)
+    da = torch.zeros((2, n), device="cuda", dtype=torch.float32)
+    for k in range(case.steps, 0, -1):
+        st = s.L.lbm_cde_adjoint_step(s.h, k, mu.data_ptr(), mu_prev.data_ptr(), states[k - 1].data_ptr(),
+                                      acc.data_ptr(), da.data_ptr())
+        assert st == N.LBM_OK, s.L.lbm_cde_last_error(s.h)
+        mu, mu_prev = mu_prev, mu
+    s.sync()
+    mu0 = mu.cpu().numpy().astype(np.float64)
+    pairs = acc.cpu().numpy().astype(np.float64).reshape(ng, 2)
+    gsum = np.ascontiguousarray(pairs[:, 0] + pairs[:, 1])
+    dD = np.zeros((2, 2))
+    st = s.L.lbm_cde_grad_rates(s.h, gsum.ctypes.data_as(N._DP), dD.ctypes.data_as(N._DP), None)
+    assert st == N.LBM_OK
+    s.close()
+    assert np.abs(dD - dD_ref).max() <= 1e-5 * np.abs(dD_ref).max()
+    # backward also adds the initial-state term of B_0 = f^eq(phi0, u(0)):
+    # dL/da_d += s_d(0) phi0 sum_i mu_0,i k_i e_i,d  (k = 1/3 on the axes, 1/12 on the diagonals)
+    ex = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=np.float64)
+    ey = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=np.float64)
+    kk = np.array([0, 1 / 3, 1 / 3, 1 / 3, 1 / 3, 1 / 12, 1 / 12, 1 / 12, 1 / 12])
+    p0 = phi0.astype(np.float64).reshape(-1)
+    init = np.stack([sched[0, d] * p0 * ((kk * e)[:, None] * mu0).sum(axis=0) for d, e in enumerate((ex, ey))])
+    da = da.cpu().numpy().astype(np.float64) + init
+    ref = da_ref.cpu().numpy().astype(np.float64).reshape(2, -1)
+    assert rel_l2(da, ref) < 1e-5
