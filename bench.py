@@ -344,9 +344,10 @@ def e2e_run(store: str, steps: int):
             "note": f"one lbm_cde_run_host call of {steps} steps; per-step bytes are the call's copies / steps"}
 
 
-def d3q15_bench(steps: int):
+def d3q15_bench(steps: int, storage: str = "f32"):
     """The D3Q15 workload: 384^3 periodic, divergence-free random velocity field,
-    full anisotropic D, FP32 (132 B per lattice update)."""
+    full anisotropic D; FP32 state (132 B per lattice update) or 16-bit offsets
+    (15 x 2 x 2 + 2 x 4 phi + 12 u = 80 B)."""
     import torch
 
     from paper_1404_2363_gb300 import workloads as W
@@ -354,7 +355,7 @@ def d3q15_bench(steps: int):
 
     n = 384
     wl = W.d3q15_workload(n)
-    s = Solver(lattice=15, nx=n, ny=n, nz=n)
+    s = Solver(lattice=15, nx=n, ny=n, nz=n, storage=storage)
     s.set_D(wl["D"])
     s.set_velocity(torch.from_numpy(wl["u"].astype(np.float32)).cuda())
     s.set_phi(torch.from_numpy(wl["phi0"].astype(np.float32)).cuda())
@@ -365,9 +366,10 @@ def d3q15_bench(steps: int):
     s.close()
     peak, kind = peaks()
     cells = n ** 3
-    gbs = cells * 132 / (dt / k) / 1e9
-    return {"grid": [n, n, n], "steps": k, "MLUPS": cells * k / dt / 1e6, "bytes_per_lu": 132,
-            "achieved_gbs": gbs, f"frac_of_{kind}_hbm": gbs / peak,
+    blu = 132 if storage == "f32" else 80
+    gbs = cells * blu / (dt / k) / 1e9
+    return {"grid": [n, n, n], "storage": storage, "steps": k, "MLUPS": cells * k / dt / 1e6,
+            "bytes_per_lu": blu, "achieved_gbs": gbs, f"frac_of_{kind}_hbm": gbs / peak,
             "launch": {"block": shape[0], "vec": shape[1]}}
 
 
@@ -541,6 +543,8 @@ def main():
     torch.cuda.empty_cache()
 
     variants["d3q15_384"] = d3q15_bench(args.steps)
+    torch.cuda.empty_cache()
+    variants["d3q15_384_bf16"] = d3q15_bench(args.steps, "bf16")
     torch.cuda.empty_cache()
     variants["taylor_aris_batch"] = batch_bench(args.steps)
     torch.cuda.empty_cache()
