@@ -45,7 +45,8 @@ def peaks():
         return 6800.0, "fallback"
 
 
-STEP_SOURCES = ["lbm_internal.cuh", "lbm_device.cuh", "lbm_step_inst.cuh", "step_d2q9_f32.cu"]
+STEP_SOURCES = ["lbm_internal.cuh", "lbm_device.cuh", "lbm_d3q15.cuh", "lbm_pair.cuh", "lbm_pair_d3q15.cuh",
+                "lbm_step_inst.cuh", "step_d2q9_f32.cu"]
 
 
 def kernel_source_hash():
@@ -545,6 +546,8 @@ def main():
     variants["d3q15_384"] = d3q15_bench(args.steps)
     torch.cuda.empty_cache()
     variants["d3q15_384_bf16"] = d3q15_bench(args.steps, "bf16")
+    torch.cuda.empty_cache()
+    variants["d3q15_384_f16"] = d3q15_bench(args.steps, "f16")
     torch.cuda.empty_cache()
     variants["taylor_aris_batch"] = batch_bench(args.steps)
     torch.cuda.empty_cache()

@@ -168,21 +168,23 @@ lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps);
 
 /* Sets the launch shape of the step kernel: block threads per CTA along x
  * (a multiple of 32 in [32, 256]) and vec cells per thread (1 or 2; for the
- * D2Q9 16-bit storage forms, 3 selects the row-walking kernel, 4 the
- * shared-memory tile kernel, which needs nx % 32 == 0 and ny % 8 == 0, and 5
- * the node-pair kernel (two adjacent nodes per thread in paired FP32
- * arithmetic), which needs nx even and 12 ncell < 2^31; for D2Q9 with any
- * storage, 6 selects the node-quad kernel: four nodes per thread, 128-bit
- * (FP32) or 64-bit (16-bit) vector loads and stores, which needs nx % 4 == 0,
- * 12 ncell < 2^31 and a 16-byte aligned velocity field; other fields fall back
- * to the one-node kernel).
+ * D2Q9 16-bit storage forms, 3 selects the row-walking kernel and 4 the
+ * shared-memory tile kernel, which needs nx % 32 == 0 and ny % 8 == 0; for
+ * the 16-bit storage forms of both lattices, 5 selects the node-pair kernel
+ * (two adjacent nodes per thread in paired FP32 arithmetic), which needs nx
+ * even, (q + 3) ncell < 2^31 and an 8-byte aligned velocity field; for D2Q9
+ * with any storage, 6 selects the node-quad kernel: four nodes per thread,
+ * 128-bit (FP32) or 64-bit (16-bit) vector loads and stores, which needs
+ * nx % 4 == 0, 12 ncell < 2^31 and a 16-byte aligned velocity field; a shape
+ * whose field does not meet these runs the one-node kernel).
  * Results do not depend on the shape beyond FP32 rounding order. Errors:
  * LBM_E_ARG. */
 lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec);
 
 /* Autotuner: times every launch shape (block 64/128/256 x vec 1/2, the node-quad
- * kernel for D2Q9, and the row-walking, tile and node-pair kernels for D2Q9
- * 16-bit storage) over `steps` steps from the
+ * kernel for D2Q9, the row-walking, tile and node-pair kernels for D2Q9
+ * 16-bit storage, the node-pair kernel at 64 .. 256 threads for D3Q15 16-bit
+ * storage) over `steps` steps from the
  * current state, keeps the fastest, and restores the state and step count.
  * With LBMCDE_TUNE_CACHE set, the choice is read from / appended to that text
  * file (lines "key block vec"; the key holds lattice, storage, grid, velocity

@@ -446,15 +446,15 @@ lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec)
 {
     if (!h) return fail(h, LBM_E_ARG, "NULL handle");
     const bool tile_ok = h->d.nx % 32 == 0 && h->d.ny % 8 == 0;
-    const bool pair_ok = h->d.nx % 2 == 0 && 12LL * h->ncell < (1LL << 31);
+    const bool pair_ok = h->neq && h->d.nx % 2 == 0 && (long long)(h->q + 3) * h->ncell < (1LL << 31);
     const bool quad = h->q == 9 && h->d.nx % 4 == 0 && 12LL * h->ncell < (1LL << 31);
     if (block < 32 || block > 256 || block % 32 != 0 || vec < 1 || vec > 6 ||
-        (vec >= 3 && vec <= 5 && !(h->q == 9 && h->neq)) || (vec == 4 && !tile_ok) || (vec == 5 && !pair_ok) ||
+        (vec >= 3 && vec <= 4 && !(h->q == 9 && h->neq)) || (vec == 4 && !tile_ok) || (vec == 5 && !pair_ok) ||
         (vec == 6 && !quad))
         return fail(h, LBM_E_ARG, "block must be a multiple of 32 in [32, 256]; vec 1 or 2 "
                                   "(3: row-walking kernel, 4: shared-memory tile kernel with nx % 32 == 0 "
-                                  "and ny % 8 == 0, 5: node-pair kernel with nx even; 3-5 D2Q9 16-bit "
-                                  "storage only; 6: D2Q9 node-quad kernel with nx % 4 == 0)");
+                                  "and ny % 8 == 0, both D2Q9 16-bit storage only; 5: node-pair kernel "
+                                  "with nx even, 16-bit storage; 6: D2Q9 node-quad kernel with nx % 4 == 0)");
     h->cfg.block = block;
     h->cfg.vec = vec;
     return LBM_OK;
@@ -539,7 +539,8 @@ lbm_status lbm_cde_autotune(lbm_cde_t h, int64_t steps, int32_t* block_out, int3
     cudaEventCreate(&e1);
     // candidates: generic kernel (1 or 2 nodes per thread) at 64/128/256 threads;
     // for D2Q9 16-bit storage also the row-walking and tile kernels (one shape
-    // each) and the node-pair kernel at 64/128/256 threads
+    // each) and the node-pair kernel at 64/128/256 threads; for D3Q15 16-bit
+    // storage the node-pair kernel at 64 .. 256 threads
     std::vector<LaunchCfg> cand;
     for (int vec = 1; vec <= 2; ++vec)
         for (int b : {64, 128, 256}) cand.push_back(LaunchCfg{b, vec});
@@ -549,6 +550,8 @@ lbm_status lbm_cde_autotune(lbm_cde_t h, int64_t steps, int32_t* block_out, int3
         if (h->d.nx % 2 == 0 && 12LL * h->ncell < (1LL << 31))
             for (int b : {64, 128, 256}) cand.push_back(LaunchCfg{b, 5});
     }
+    if (h->q == 15 && h->neq && h->d.nx % 2 == 0 && 18LL * h->ncell < (1LL << 31))
+        for (int b : {64, 96, 128, 192, 256}) cand.push_back(LaunchCfg{b, 5});
     if (h->q == 9 && h->d.nx % 4 == 0 && 12LL * h->ncell < (1LL << 31))
         for (int b : {64, 128, 256}) cand.push_back(LaunchCfg{b, 6});
     for (size_t ci = 0; ci < cand.size() && s == LBM_OK; ++ci) {

@@ -97,6 +97,10 @@ __host__ __device__ constexpr int row_norm2(int k) {
     return s;
 }
 
+}  // namespace lbm
+#include "lbm_d3q15.cuh"   // D3Q15 moment maps and collision (one node or a node pair)
+namespace lbm {
+
 template <class L>
 __host__ __device__ constexpr int mirror_y(int i) {
     for (int j = 0; j < L::Q; ++j)
@@ -213,7 +217,8 @@ __device__ __forceinline__ float int_dot(Wf W, const float* v)
 // ---------------------------------------------------------------------------
 // The integer maps m = M v and v = M^T a. For D2Q9 both are evaluated as
 // sums and differences of the populations that share |e| (24 operations each
-// instead of the 50-58 of the row-by-row chains); D3Q15 uses the row chains.
+// instead of the 50-58 of the row-by-row chains); D3Q15 as the butterflies of
+// lbm_d3q15.cuh.
 // ---------------------------------------------------------------------------
 template <class L>
 __device__ __forceinline__ void moments(const float (&v)[L::Q], float (&m)[L::Q])
@@ -236,8 +241,7 @@ __device__ __forceinline__ void moments(const float (&v)[L::Q], float (&m)[L::Q]
         m[7] = sx - sy;
         m[8] = p57 - p68;
     } else {
-#pragma unroll
-        for (int k = 0; k < L::Q; ++k) m[k] = int_dot<L::Q>([k](int i) { return L::M(k, i); }, v);
+        d3q15_moments<float>(v, m);
     }
 }
 
@@ -267,14 +271,7 @@ __device__ __forceinline__ float populations(const float (&a)[L::Q], float (&v)[
         if (FULL) v[0] = ZERO0 ? __fmul_rn(4.f, a[2] - a[1]) : fmaf(4.f, a[2], fmaf(-4.f, a[1], a[0]));
         return __fmul_rn(4.f, A + B);
     } else {
-        float sum = 0.f;
-#pragma unroll
-        for (int i = 1; i < L::Q; ++i) {
-            v[i] = int_dot<L::Q>([i](int k) { return (ZERO0 && k == 0) ? 0 : L::M(k, i); }, a);
-            sum += v[i];
-        }
-        if (FULL) v[0] = int_dot<L::Q>([](int k) { return (ZERO0 && k == 0) ? 0 : L::M(k, 0); }, a);
-        return sum;
+        return d3q15_populations<float, ZERO0, FULL>(a, v);
     }
 }
 
@@ -290,6 +287,7 @@ __device__ __forceinline__ float collide(float (&f)[L::Q], float ux, float uy, f
                                          const CC& c)
 {
     constexpr int Q = L::Q;
+    if constexpr (L::Q == 15) return collide_d3q15<float, OFFSET>(f, ux, uy, uz, c);   // MRT-A only
     float m[Q];
     moments<L>(f, m);
     const float phi = m[0];

@@ -119,6 +119,14 @@ inline bool quad_ok(const StepArgs& a, int ukind)
            (ukind != U_FIELD || (reinterpret_cast<uintptr_t>(a.ua) & 15) == 0);
 }
 
+// The node-pair kernels need nx even, int offsets ((q + 3) ncell < 2^31) and
+// an 8-byte aligned velocity field (they read two nodes per vector load).
+inline bool pair_ok(const StepArgs& a, int ukind, int q)
+{
+    return a.nx % 2 == 0 && (long long)(q + 3) * a.ncell < (1LL << 31) &&
+           (ukind != U_FIELD || (reinterpret_cast<uintptr_t>(a.ua) & 7) == 0);
+}
+
 struct LaunchCfg {
     int block;   // threads per block (multiple of 32)
     int vec;     // cells per thread along x (1, 2 or 4)

@@ -3,6 +3,7 @@
 // LBM_FN defined, so the template instantiations compile in parallel.
 #include "lbm_device.cuh"
 #include "lbm_pair.cuh"
+#include "lbm_pair_d3q15.cuh"
 
 namespace lbm {
 
@@ -18,8 +19,17 @@ static cudaError_t step_vec(LaunchCfg cfg, const StepArgs& a, cudaStream_t st)
             return cudaGetLastError();
         }
     }
+    if constexpr (L::Q == 15 && STORE != ST_F32) {
+        if (cfg.vec == 5 && pair_ok(a, UK, L::Q)) {
+            // node-pair variant (paired FP32 arithmetic, two adjacent nodes per thread)
+            const int per = 2 * cfg.block;
+            dim3 grid((unsigned)((a.nx + per - 1) / per), (unsigned)a.ny, (unsigned)a.nz);
+            k_step_pair_d3q15<STORE, UK, WALLS><<<grid, cfg.block, 0, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (L::Q == 9 && STORE != ST_F32) {
-        if (cfg.vec == 5 && a.nx % 2 == 0 && a.nz == 1 && 12LL * a.ncell < (1LL << 31)) {
+        if (cfg.vec == 5 && a.nz == 1 && pair_ok(a, UK, L::Q)) {
             // node-pair variant (paired FP32 arithmetic, two adjacent nodes per thread)
             const int per = 2 * cfg.block;
             dim3 grid((unsigned)((a.nx + per - 1) / per), (unsigned)a.ny, 1);

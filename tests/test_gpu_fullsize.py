@@ -52,10 +52,16 @@ def test_vortex_4096_windows(O, storage, tol, launch):
         assert rel_l2(got[np.ix_(iy, ix)][c, c], want[c, c]) <= tol, (x0, y0)
 
 
-def test_d3q15_384_windows(O):
+@pytest.mark.parametrize("storage,tol,launch", [("f32", 1e-5, None), ("f16", 2e-3, (64, 5)),
+                                               ("bf16", 2e-3, (192, 5)), ("bf16", 2e-3, (128, 1))])
+def test_d3q15_384_windows(O, storage, tol, launch):
+    """launch (., 5): the D3Q15 node-pair kernel of the 16-bit forms (the
+    autotuner's choice for them on this workload); (., 1) the one-node kernel."""
     N, nsteps, half = 384, 8, 14
     wl = W.d3q15_workload(N)
-    s = Solver(lattice=15, nx=N, ny=N, nz=N)
+    s = Solver(lattice=15, nx=N, ny=N, nz=N, storage=storage)
+    if launch:
+        s.set_launch(*launch)
     s.set_D(wl["D"])
     u = wl["u"].astype(np.float32)
     s.set_velocity(torch.from_numpy(u).cuda())
@@ -74,7 +80,36 @@ def test_d3q15_384_windows(O):
         p = O.default_params_3d(nx=n, ny=n, nz=n, A=O.A_from_D(wl["D"], q=15, alpha1=-1.2, alpha2=192.0))
         want = O.run(p, p0.astype(np.float64)[np.ix_(iz, iy, ix)].reshape(-1), nsteps, u=wu).reshape(n, n, n)
         c = slice(half - keep, half + keep + 1)
-        assert rel_l2(got[np.ix_(iz, iy, ix)][c, c, c], want[c, c, c]) <= 1e-5
+        assert rel_l2(got[np.ix_(iz, iy, ix)][c, c, c], want[c, c, c]) <= tol, (x0, y0, z0)
+
+
+@pytest.mark.parametrize("storage,launch", [("f32", None), ("f16", (64, 5)), ("bf16", (64, 5)),
+                                            ("f16", (64, 1)), ("bf16", (64, 1))])
+def test_d3q15_1000_steps_error_vs_fp64(O, storage, launch):
+    """The D3Q15 workload's recipe (random rotated anisotropic D, divergence-free
+    random u, Gaussian hill) on a 48^3 grid for 1000 steps: relative L2 error of
+    phi against FP64 and the change of the total (conserved exactly by the scheme)
+    stay within the bounds of the D2Q9 5000-step test."""
+    n, steps = 48, 1000
+    wl = W.d3q15_workload(n)
+    u = wl["u"].astype(np.float32)
+    p0 = wl["phi0"].astype(np.float32)
+    s = Solver(lattice=15, nx=n, ny=n, nz=n, storage=storage)
+    if launch:
+        s.set_launch(*launch)
+    s.set_D(wl["D"])
+    s.set_velocity(torch.from_numpy(u).cuda())
+    s.set_phi(torch.from_numpy(p0).cuda())
+    s.step(steps)
+    got = s.get_phi().cpu().numpy().astype(np.float64)
+    s.close()
+    p = O.default_params_3d(nx=n, ny=n, nz=n, A=O.A_from_D(wl["D"], q=15, alpha1=-1.2, alpha2=192.0))
+    want = O.run(p, p0.astype(np.float64).reshape(-1), steps, u=u.astype(np.float64).reshape(3, -1)).reshape(n, n, n)
+    err = rel_l2(got, want)
+    mass = abs(got.sum() - p0.astype(np.float64).sum()) / p0.astype(np.float64).sum()
+    print(f"D3Q15 {storage} {launch}: relative L2 error after {steps} steps = {err:.3e}, mass change {mass:.2e}")
+    assert err <= {"f32": 1e-5, "f16": 1e-4, "bf16": 2e-3}[storage]
+    assert mass <= {"f32": 1e-6, "f16": 1e-5, "bf16": 2e-4}[storage]
 
 
 @pytest.mark.parametrize("storage,tol,launch", [("f32", 1e-5, None), ("f16", 2e-3, None), ("bf16", 2e-3, None),

@@ -184,12 +184,49 @@ def test_quad_kernel_narrow_grids(O, nx, ny):
         assert rel_l2(got, want) <= TOL[storage], (storage, nx, ny)
 
 
+D3 = np.array([[0.03, 0.005, -0.004], [0.005, 0.025, 0.003], [-0.004, 0.003, 0.035]])
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("bc,ukind", [(("periodic", "periodic"), "field"), (("noflux", "noflux"), "row"),
+                                      (("bounceback", "bounceback"), "field"),
+                                      (("dirichlet", "dirichlet"), "field"), (("periodic", "periodic"), "none")])
+def test_pair_offset_kernel_d3q15(O, storage, bc, ukind):
+    """The D3Q15 node-pair kernel of the 16-bit forms (launch vec = 5: paired FP32
+    decode, collision and store) against the oracle on a 70 x 13 x 9 grid (35
+    pairs per row: two 32-thread blocks, the second ragged), and against the
+    one-node kernel (same operations up to the folding of the schedule factor into
+    the decode slopes and the compiler's fusing of paired multiply-adds)."""
+    case = Case(lattice=15, storage=storage, bc=bc, ukind=ukind, sched=ukind != "none", nx=70, ny=13, nz=9,
+                steps=40, D=D3, phi_w=(1.0, 0.25) if bc[0] == "dirichlet" else (0.0, 0.0))
+    phi0, a, sched = case.inputs()
+    got, _ = _run_vec3(case, phi0, a, sched, vec=5, block=32)
+    want = run_oracle(O, case, phi0, a, sched)
+    assert rel_l2(got, want) <= TOL[storage]
+    one, _ = _run_vec3(case, phi0, a, sched, vec=1, block=64)
+    assert rel_l2(got, one) <= TOL[storage] / 4
+    if bc[0] == "dirichlet":
+        assert np.abs(got[:, 0] - 1.0).max() < 1e-4 and np.abs(got[:, -1] - 0.25).max() < 1e-4
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(2, 5, 3), (4, 3, 4), (66, 4, 3)])
+def test_pair_offset_kernel_d3q15_narrow_grids(O, nx, ny, nz):
+    """One pair per row (both shifted pulls wrap onto the same pair), two pairs,
+    and 33 pairs with 32-thread blocks (a second block of one thread)."""
+    for storage in ("f16", "bf16"):
+        case = Case(lattice=15, storage=storage, nx=nx, ny=ny, nz=nz, steps=30, D=D3)
+        phi0, a, sched = case.inputs()
+        got, _ = _run_vec3(case, phi0, a, sched, vec=5, block=32)
+        want = run_oracle(O, case, phi0, a, sched)
+        assert rel_l2(got, want) <= TOL[storage], (storage, nx, ny, nz)
+
+
 def _run_vec3(case, phi0, a, sched, vec=3, block=256):
     import torch
     from paper_1404_2363_gb300.solver import Solver
 
-    s = Solver(nx=case.nx, ny=case.ny, storage=case.storage, bc=case.bc, phi_w=case.phi_w,
-               model=case.model)
+    s = Solver(lattice=case.lattice, nx=case.nx, ny=case.ny, nz=case.nz, storage=case.storage, bc=case.bc,
+               phi_w=case.phi_w, model=case.model)
     s.set_launch(block, vec)
     s.set_D(case.D)
     if a is not None:
