@@ -175,16 +175,28 @@ lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps);
  * even, (q + 3) ncell < 2^31 and an 8-byte aligned velocity field; for D2Q9
  * with any storage, 6 selects the node-quad kernel: four nodes per thread,
  * 128-bit (FP32) or 64-bit (16-bit) vector loads and stores, which needs
- * nx % 4 == 0, 12 ncell < 2^31 and a 16-byte aligned velocity field; a shape
+ * nx % 4 == 0, 12 ncell < 2^31 and a 16-byte aligned velocity field; for
+ * the D2Q9 16-bit storage forms, vec 7 with block 128 selects the TMA-staged
+ * kernel: persistent CTAs walk 256-column strips row by row, the source rows
+ * arrive in a shared-memory ring through tensor copies, which needs
+ * nx % 256 == 0, 12 ncell < 2^31 and a 16-byte aligned velocity field; a shape
  * whose field does not meet these runs the one-node kernel).
  * Results do not depend on the shape beyond FP32 rounding order. Errors:
  * LBM_E_ARG. */
 lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec);
 
+/* Bound on each device-side wait of the TMA-staged kernel (launch vec 7), in SM
+ * clock cycles (default 4e9, about 2 s; 0 gives up at once). A wait that runs
+ * out latches LBM_E_TIMEOUT, the kernel stops computing, waits (bounded) for
+ * its copies in flight and returns; lbm_cde_sum_phi / lbm_cde_sync report the
+ * status and clear it, and the handle stays usable. Errors: LBM_E_ARG
+ * (cycles < 0). */
+lbm_status lbm_cde_set_wait_limit(lbm_cde_t h, int64_t cycles);
+
 /* Autotuner: times every launch shape (block 64/128/256 x vec 1/2, the node-quad
- * kernel for D2Q9, the row-walking, tile and node-pair kernels for D2Q9
- * 16-bit storage, the node-pair kernel at 64 .. 256 threads for D3Q15 16-bit
- * storage) over `steps` steps from the
+ * kernel for D2Q9, the row-walking, tile, node-pair and TMA-staged kernels for
+ * D2Q9 16-bit storage, the node-pair kernel at 64 .. 256 threads for D3Q15
+ * 16-bit storage) over `steps` steps from the
  * current state, keeps the fastest, and restores the state and step count.
  * With LBMCDE_TUNE_CACHE set, the choice is read from / appended to that text
  * file (lines "key block vec"; the key holds lattice, storage, grid, velocity

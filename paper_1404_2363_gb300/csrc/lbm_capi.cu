@@ -53,6 +53,13 @@ struct lbm_cde_s {
     float2* grad_acc = nullptr;
     float* phi0_saved = nullptr;
     bool have_fwd = false;
+    // TMA-staged D2Q9 step (launch vec 7): tensor maps per source buffer, and the
+    // device status word its bounded waits report to
+    lbm::TmaMaps tmaps[2];
+    bool tmaps_ok = false;
+    const float* tmaps_ua = nullptr;
+    int* status_dev = nullptr;
+    long long wait_limit = 4000000000LL;   // SM cycles per bounded device wait (about 2 s)
 };
 
 static thread_local std::string g_create_err;
@@ -221,7 +228,37 @@ static StepArgs make_args(lbm_cde_t h, int src_idx)
     a.phiw_lo = (float)h->d.phi_w_lo_y;
     a.phiw_hi = (float)h->d.phi_w_hi_y;
     a.c = h->coef;
+    a.status = h->status_dev;
+    a.spin_limit = h->wait_limit;
     return a;
+}
+
+// Tensor maps for the TMA-staged step, re-encoded when the velocity field changes.
+static lbm_status ensure_tma_maps(lbm_cde_t h)
+{
+    const float* ua = h->ukind == LBM_U_FIELD ? h->ua : nullptr;
+    if (h->tmaps_ok && h->tmaps_ua == ua) return LBM_OK;
+    h->tmaps_ok = false;
+    for (int b = 0; b < 2; ++b)
+        if (!lbm::encode_tma_maps(h->state[b], h->phi[b], ua, (int)h->d.nx, (int)h->d.ny, &h->tmaps[b]))
+            return fail(h, LBM_E_CUDA, "tensor map encoding failed (launch vec 7)");
+    h->tmaps_ok = true;
+    h->tmaps_ua = ua;
+    return LBM_OK;
+}
+
+// The status word latched by bounded device waits: LBM_E_TIMEOUT is reported
+// (and the word cleared) by the next synchronising call.
+static lbm_status check_status(lbm_cde_t h)
+{
+    int st = 0;
+    CK(h, cudaMemcpyAsync(&st, h->status_dev, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    if (st != 0) {
+        CK(h, cudaMemsetAsync(h->status_dev, 0, sizeof(int), h->st));
+        return fail(h, (lbm_status)st, "a bounded wait in the TMA-staged step kernel timed out");
+    }
+    return LBM_OK;
 }
 
 static int ukind_internal(int k)
@@ -336,6 +373,11 @@ lbm_status lbm_cde_create(const lbm_cde_desc* desc, lbm_cde_t* out)
         return fail(nullptr, LBM_E_OOM, "scratch allocation failed");
     }
     h->sum_dev = h->partials + h->nparts;
+    h->status_dev = static_cast<int*>(dev_alloc(h, 16));
+    if (!h->status_dev || cudaMemsetAsync(h->status_dev, 0, 16, h->st) != cudaSuccess) {
+        lbm_cde_destroy(h);
+        return fail(nullptr, LBM_E_OOM, "status word allocation failed");
+    }
     // launch shape: 256 threads along x, cells per thread chosen for the row length
     h->cfg.block = d.nx >= 256 ? 256 : (d.nx >= 128 ? 128 : 64);
     h->cfg.vec = 1;
@@ -359,6 +401,7 @@ lbm_status lbm_cde_destroy(lbm_cde_t h)
     dev_free(h, h->mu[1]);
     dev_free(h, h->adj_partials);
     dev_free(h, h->phi0_saved);
+    dev_free(h, h->status_dev);
     delete h;
     return LBM_OK;
 }
@@ -433,12 +476,25 @@ lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps)
     if (!h->ready) return fail(h, LBM_E_STATE, "set_phi must come before step");
     const bool walls = h->d.bc_lo_y != LBM_BC_PERIODIC;
     const int uk = ukind_internal(h->ukind);
+    const bool tma = h->cfg.vec == 7 && h->q == 9 && h->neq;
+    if (tma) {
+        const lbm_status ts = ensure_tma_maps(h);
+        if (ts != LBM_OK) return ts;
+    }
     for (int64_t n = 0; n < nsteps; ++n) {
         StepArgs a = make_args(h, h->cur);
+        if (tma) a.tma = &h->tmaps[h->cur];
         CK(h, lbm::launch_step(h->q, h->d.storage, uk, walls, h->cfg, a, h->st));
         h->cur ^= 1;
         h->t += 1;
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_set_wait_limit(lbm_cde_t h, int64_t cycles)
+{
+    if (!h || cycles < 0) return fail(h, LBM_E_ARG, "bad argument");
+    h->wait_limit = cycles;
     return LBM_OK;
 }
 
@@ -448,6 +504,14 @@ lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec)
     const bool tile_ok = h->d.nx % 32 == 0 && h->d.ny % 8 == 0;
     const bool pair_ok = h->neq && h->d.nx % 2 == 0 && (long long)(h->q + 3) * h->ncell < (1LL << 31);
     const bool quad = h->q == 9 && h->d.nx % 4 == 0 && 12LL * h->ncell < (1LL << 31);
+    const bool tma = h->q == 9 && h->neq && h->d.nx % 256 == 0 && 12LL * h->ncell < (1LL << 31);
+    if (vec == 7) {
+        if (block != 128 || !tma)
+            return fail(h, LBM_E_ARG, "vec 7 (TMA-staged D2Q9 16-bit kernel) needs block 128 and nx % 256 == 0");
+        h->cfg.block = block;
+        h->cfg.vec = vec;
+        return LBM_OK;
+    }
     if (block < 32 || block > 256 || block % 32 != 0 || vec < 1 || vec > 6 ||
         (vec >= 3 && vec <= 4 && !(h->q == 9 && h->neq)) || (vec == 4 && !tile_ok) || (vec == 5 && !pair_ok) ||
         (vec == 6 && !quad))
@@ -554,6 +618,9 @@ lbm_status lbm_cde_autotune(lbm_cde_t h, int64_t steps, int32_t* block_out, int3
         for (int b : {64, 96, 128, 192, 256}) cand.push_back(LaunchCfg{b, 5});
     if (h->q == 9 && h->d.nx % 4 == 0 && 12LL * h->ncell < (1LL << 31))
         for (int b : {64, 128, 256}) cand.push_back(LaunchCfg{b, 6});
+    if (h->q == 9 && h->neq && h->d.nx % 256 == 0 && 12LL * h->ncell < (1LL << 31) &&
+        ensure_tma_maps(h) == LBM_OK)   // tensor maps available
+        cand.push_back(LaunchCfg{128, 7});
     for (size_t ci = 0; ci < cand.size() && s == LBM_OK; ++ci) {
         h->cfg = cand[ci];
         s = lbm_cde_set_state(h, save, t0);
@@ -605,7 +672,8 @@ lbm_status lbm_cde_sum_phi(lbm_cde_t h, double* out_host)
     StepArgs a = make_args(h, h->cur);
     CK(h, lbm::launch_sum(h->q, h->d.storage, a, h->partials, h->nparts, h->sum_dev, h->st));
     CK(h, cudaMemcpyAsync(out_host, h->sum_dev, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    CK(h, cudaStreamSynchronize(h->st));
+    const lbm_status ds = check_status(h);   // synchronises
+    if (ds != LBM_OK) return ds;
     if (!std::isfinite(*out_host)) return fail(h, LBM_E_NONFINITE, "sum of phi is not finite");
     return LBM_OK;
 }
@@ -613,8 +681,7 @@ lbm_status lbm_cde_sum_phi(lbm_cde_t h, double* out_host)
 lbm_status lbm_cde_sync(lbm_cde_t h)
 {
     if (!h) return fail(h, LBM_E_ARG, "NULL handle");
-    CK(h, cudaStreamSynchronize(h->st));
-    return LBM_OK;
+    return check_status(h);
 }
 
 lbm_status lbm_cde_state_bytes(lbm_cde_t h, size_t* bytes_out)

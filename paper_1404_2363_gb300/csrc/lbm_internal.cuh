@@ -2,6 +2,7 @@
 // Not part of the public C ABI (include/lbm_cde.h).
 #pragma once
 
+#include <cuda.h>            // CUtensorMap (tensor maps of the TMA-staged step)
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -56,6 +57,14 @@ inline void fold_offset_coef(Coef& c)
     }
 }
 
+// Tensor maps of the TMA-staged D2Q9 step (k_step_tma_d2q9) for one source
+// buffer: each pair is the 256-column box of one grid row and its halo box.
+struct TmaMaps {
+    CUtensorMap g, gh;    // 16-bit offsets [9][ny][nx]: boxes (256, 1, 9) and (8, 1, 9)
+    CUtensorMap p, ph;    // phi [ny][nx]: boxes (256, 1) and (4, 1)
+    CUtensorMap u, uh;    // velocity factors [2][ny][nx]: boxes (256, 1, 2) and (4, 1, 2)
+};
+
 struct StepArgs {
     const void* src;      // state planes [q][ncell] (float or 16-bit)
     void* dst;
@@ -72,6 +81,9 @@ struct StepArgs {
     int bc_lo, bc_hi;
     float phiw_lo, phiw_hi;
     Coef c;
+    int* status;          // device status word (LBM_E_TIMEOUT from a bounded wait) or nullptr
+    long long spin_limit; // SM clock cycles a bounded wait may take (0: give up at once)
+    const TmaMaps* tma;   // host pointer: tensor maps of src / phi_src / ua, or nullptr
 };
 
 // One reverse-time step (lbm_adjoint.cu).
@@ -126,6 +138,18 @@ inline bool pair_ok(const StepArgs& a, int ukind, int q)
     return a.nx % 2 == 0 && (long long)(q + 3) * a.ncell < (1LL << 31) &&
            (ukind != U_FIELD || (reinterpret_cast<uintptr_t>(a.ua) & 7) == 0);
 }
+
+// The TMA-staged D2Q9 kernel needs 256-column strips (nx % 256 == 0), int
+// offsets, a 16-byte aligned velocity field and the tensor maps of the source.
+inline bool tma_ok(const StepArgs& a, int ukind)
+{
+    return a.tma != nullptr && a.nx % 256 == 0 && a.nz == 1 && 12LL * a.ncell < (1LL << 31) &&
+           (ukind != U_FIELD || (reinterpret_cast<uintptr_t>(a.ua) & 15) == 0);
+}
+
+// Encodes the tensor maps for one source buffer (lbm_tma.cu); false if the
+// driver entry point is missing or the layout breaks a tensor-map rule.
+bool encode_tma_maps(const void* g, const float* phi, const float* ua, int nx, int ny, TmaMaps* out);
 
 struct LaunchCfg {
     int block;   // threads per block (multiple of 32)

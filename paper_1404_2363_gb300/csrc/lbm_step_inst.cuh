@@ -4,6 +4,7 @@
 #include "lbm_device.cuh"
 #include "lbm_pair.cuh"
 #include "lbm_pair_d3q15.cuh"
+#include "lbm_tma_d2q9.cuh"
 
 namespace lbm {
 
@@ -29,6 +30,7 @@ static cudaError_t step_vec(LaunchCfg cfg, const StepArgs& a, cudaStream_t st)
         }
     }
     if constexpr (L::Q == 9 && STORE != ST_F32) {
+        if (cfg.vec == 7 && tma_ok(a, UK)) return launch_tma_d2q9<STORE, UK, WALLS>(a, st);   // TMA-staged rows
         if (cfg.vec == 5 && a.nz == 1 && pair_ok(a, UK, L::Q)) {
             // node-pair variant (paired FP32 arithmetic, two adjacent nodes per thread)
             const int per = 2 * cfg.block;

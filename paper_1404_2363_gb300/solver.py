@@ -140,6 +140,10 @@ class Solver:
     def set_launch(self, block=256, vec=1):
         self._ck(self.L.lbm_cde_set_launch(self.h, int(block), int(vec)), "lbm_cde_set_launch")
 
+    def set_wait_limit(self, cycles):
+        """Bound (SM clock cycles) on each device wait of the TMA-staged kernel."""
+        self._ck(self.L.lbm_cde_set_wait_limit(self.h, int(cycles)), "lbm_cde_set_wait_limit")
+
     def autotune(self, steps=20):
         b, v = ctypes.c_int32(), ctypes.c_int32()
         self._ck(self.L.lbm_cde_autotune(self.h, int(steps), ctypes.byref(b), ctypes.byref(v)), "lbm_cde_autotune")
@@ -166,6 +170,7 @@ class Solver:
         return v.value
 
     def sync(self):
+        """Waits for the stream; reports a latched device status (LBM_E_TIMEOUT)."""
         self._ck(self.L.lbm_cde_sync(self.h), "lbm_cde_sync")
 
     def state_bytes(self):

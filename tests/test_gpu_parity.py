@@ -184,6 +184,71 @@ def test_quad_kernel_narrow_grids(O, nx, ny):
         assert rel_l2(got, want) <= TOL[storage], (storage, nx, ny)
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("bc,ukind", [(("periodic", "periodic"), "field"), (("noflux", "noflux"), "row"),
+                                      (("bounceback", "bounceback"), "field"),
+                                      (("dirichlet", "dirichlet"), "field"), (("periodic", "periodic"), "none")])
+def test_tma_offset_kernel(O, storage, bc, ukind):
+    """The TMA-staged kernel of the D2Q9 16-bit forms (launch vec = 7: source rows
+    staged in shared memory by tensor copies, persistent CTAs) against the oracle
+    on a 512 x 37 grid (74 strip rows: one-row work ranges), and against the
+    node-pair kernel, whose arithmetic it shares."""
+    case = Case(storage=storage, bc=bc, ukind=ukind, sched=ukind != "none", nx=512, ny=37,
+                phi_w=(1.0, 0.25) if bc[0] == "dirichlet" else (0.0, 0.0))
+    phi0, a, sched = case.inputs()
+    got, s = _run_vec3(case, phi0, a, sched, vec=7, block=128)
+    s.sync()
+    want = run_oracle(O, case, phi0, a, sched)
+    assert rel_l2(got, want) <= TOL[storage]
+    pair, _ = _run_vec3(case, phi0, a, sched, vec=5, block=64)
+    assert rel_l2(got, pair) <= TOL[storage] / 4
+
+
+@pytest.mark.parametrize("nx,ny,steps", [(768, 600, 12), (256, 1, 30), (256, 3, 30), (1024, 5, 20)])
+def test_tma_kernel_work_ranges(O, nx, ny, steps):
+    """Work ranges that cross strip boundaries (768 x 600: three strips, about
+    three strip rows per CTA), a one-row and a three-row periodic grid (every
+    staged row wraps), and four strips of five rows."""
+    for storage in ("f16", "bf16"):
+        case = Case(storage=storage, nx=nx, ny=ny, steps=steps)
+        phi0, a, sched = case.inputs()
+        got, s = _run_vec3(case, phi0, a, sched, vec=7, block=128)
+        s.sync()
+        want = run_oracle(O, case, phi0, a, sched)
+        assert rel_l2(got, want) <= TOL[storage], (storage, nx, ny)
+
+
+def test_tma_wait_timeout_is_reported_and_handle_recovers(O):
+    """A zero wait limit makes every bounded wait of the TMA-staged kernel give up:
+    the step reports LBM_E_TIMEOUT on the next synchronising call, no kernel hangs,
+    and the same handle then runs correctly with the default limit."""
+    from paper_1404_2363_gb300 import _native as N
+
+    case = Case(storage="bf16", nx=512, ny=64, steps=20)
+    phi0, a, sched = case.inputs()
+    import torch
+    from paper_1404_2363_gb300.solver import Solver
+
+    s = Solver(nx=case.nx, ny=case.ny, storage="bf16")
+    s.set_launch(128, 7)
+    s.set_D(case.D)
+    s.set_velocity(torch.from_numpy(a).cuda(), torch.from_numpy(sched).cuda())
+    s.set_phi(torch.from_numpy(phi0).cuda())
+    s.set_wait_limit(0)
+    s.step(3)
+    with pytest.raises(N.LbmError) as e:
+        s.sync()
+    assert e.value.status == N.LBM_E_TIMEOUT
+    s.sync()                       # the status was cleared
+    s.set_wait_limit(4_000_000_000)
+    s.set_phi(torch.from_numpy(phi0).cuda())
+    s.step(case.steps)
+    got = s.get_phi().cpu().numpy().astype(np.float64)
+    s.sync()
+    want = run_oracle(O, case, phi0, a, sched)
+    assert rel_l2(got, want) <= TOL["bf16"]
+
+
 D3 = np.array([[0.03, 0.005, -0.004], [0.005, 0.025, 0.003], [-0.004, 0.003, 0.035]])
 
 
