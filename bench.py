@@ -46,7 +46,7 @@ def peaks():
 
 
 STEP_SOURCES = ["lbm_internal.cuh", "lbm_device.cuh", "lbm_d3q15.cuh", "lbm_pair.cuh", "lbm_pair_d3q15.cuh",
-                "lbm_step_inst.cuh", "step_d2q9_f32.cu"]
+                "lbm_tma_d2q9.cuh", "lbm_step_inst.cuh", "step_d2q9_f32.cu"]
 
 
 def kernel_source_hash():
