@@ -176,16 +176,18 @@ lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps);
  * with any storage, 6 selects the node-quad kernel: four nodes per thread,
  * 128-bit (FP32) or 64-bit (16-bit) vector loads and stores, which needs
  * nx % 4 == 0, 12 ncell < 2^31 and a 16-byte aligned velocity field; for
- * the D2Q9 16-bit storage forms, vec 7 with block 128 selects the TMA-staged
- * kernel: persistent CTAs walk 256-column strips row by row, the source rows
- * arrive in a shared-memory ring through tensor copies, which needs
- * nx % 256 == 0, 12 ncell < 2^31 and a 16-byte aligned velocity field; a shape
- * whose field does not meet these runs the one-node kernel).
+ * the D2Q9 16-bit storage forms, vec 7 or 8 with block 128 selects the
+ * TMA-staged kernel: CTAs walk row ranges of 256-column strips, the source
+ * rows arrive in a shared-memory ring through tensor copies (vec 7: two rows
+ * per iteration, 256 threads, six stages; vec 8: one row, 128 threads, four
+ * stages), which needs nx % 256 == 0, 12 ncell < 2^31 and a 16-byte aligned
+ * velocity field; a shape whose field does not meet these runs the one-node
+ * kernel).
  * Results do not depend on the shape beyond FP32 rounding order. Errors:
  * LBM_E_ARG. */
 lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec);
 
-/* Bound on each device-side wait of the TMA-staged kernel (launch vec 7), in SM
+/* Bound on each device-side wait of the TMA-staged kernel (launch vec 7 / 8), in SM
  * clock cycles (default 4e9, about 2 s; 0 gives up at once). A wait that runs
  * out latches LBM_E_TIMEOUT, the kernel stops computing, waits (bounded) for
  * its copies in flight and returns; lbm_cde_sum_phi / lbm_cde_sync report the

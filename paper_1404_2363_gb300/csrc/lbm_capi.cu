@@ -241,7 +241,7 @@ static lbm_status ensure_tma_maps(lbm_cde_t h)
     h->tmaps_ok = false;
     for (int b = 0; b < 2; ++b)
         if (!lbm::encode_tma_maps(h->state[b], h->phi[b], ua, (int)h->d.nx, (int)h->d.ny, &h->tmaps[b]))
-            return fail(h, LBM_E_CUDA, "tensor map encoding failed (launch vec 7)");
+            return fail(h, LBM_E_CUDA, "tensor map encoding failed (launch vec 7 / 8)");
     h->tmaps_ok = true;
     h->tmaps_ua = ua;
     return LBM_OK;
@@ -476,7 +476,7 @@ lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps)
     if (!h->ready) return fail(h, LBM_E_STATE, "set_phi must come before step");
     const bool walls = h->d.bc_lo_y != LBM_BC_PERIODIC;
     const int uk = ukind_internal(h->ukind);
-    const bool tma = h->cfg.vec == 7 && h->q == 9 && h->neq;
+    const bool tma = (h->cfg.vec == 7 || h->cfg.vec == 8) && h->q == 9 && h->neq;
     if (tma) {
         const lbm_status ts = ensure_tma_maps(h);
         if (ts != LBM_OK) return ts;
@@ -505,9 +505,9 @@ lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec)
     const bool pair_ok = h->neq && h->d.nx % 2 == 0 && (long long)(h->q + 3) * h->ncell < (1LL << 31);
     const bool quad = h->q == 9 && h->d.nx % 4 == 0 && 12LL * h->ncell < (1LL << 31);
     const bool tma = h->q == 9 && h->neq && h->d.nx % 256 == 0 && 12LL * h->ncell < (1LL << 31);
-    if (vec == 7) {
+    if (vec == 7 || vec == 8) {
         if (block != 128 || !tma)
-            return fail(h, LBM_E_ARG, "vec 7 (TMA-staged D2Q9 16-bit kernel) needs block 128 and nx % 256 == 0");
+            return fail(h, LBM_E_ARG, "vec 7 / 8 (TMA-staged D2Q9 16-bit kernel) needs block 128 and nx % 256 == 0");
         h->cfg.block = block;
         h->cfg.vec = vec;
         return LBM_OK;
@@ -619,8 +619,10 @@ lbm_status lbm_cde_autotune(lbm_cde_t h, int64_t steps, int32_t* block_out, int3
     if (h->q == 9 && h->d.nx % 4 == 0 && 12LL * h->ncell < (1LL << 31))
         for (int b : {64, 128, 256}) cand.push_back(LaunchCfg{b, 6});
     if (h->q == 9 && h->neq && h->d.nx % 256 == 0 && 12LL * h->ncell < (1LL << 31) &&
-        ensure_tma_maps(h) == LBM_OK)   // tensor maps available
+        ensure_tma_maps(h) == LBM_OK) {   // tensor maps available
         cand.push_back(LaunchCfg{128, 7});
+        cand.push_back(LaunchCfg{128, 8});
+    }
     for (size_t ci = 0; ci < cand.size() && s == LBM_OK; ++ci) {
         h->cfg = cand[ci];
         s = lbm_cde_set_state(h, save, t0);
@@ -736,8 +738,7 @@ lbm_status lbm_cde_run_host(lbm_cde_t h, const float* phi0_host, int64_t nsteps,
     s = lbm_cde_get_phi(h, h->phi_tmp);
     if (s != LBM_OK) return s;
     CK(h, cudaMemcpyAsync(phi_out_host, h->phi_tmp, bytes, cudaMemcpyDeviceToHost, h->st));
-    CK(h, cudaStreamSynchronize(h->st));
-    return LBM_OK;
+    return check_status(h);   // synchronises; reports a bounded wait that gave up
 }
 
 // ---------------------------------------------------------------------------

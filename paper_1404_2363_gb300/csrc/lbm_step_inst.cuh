@@ -30,7 +30,9 @@ static cudaError_t step_vec(LaunchCfg cfg, const StepArgs& a, cudaStream_t st)
         }
     }
     if constexpr (L::Q == 9 && STORE != ST_F32) {
-        if (cfg.vec == 7 && tma_ok(a, UK)) return launch_tma_d2q9<STORE, UK, WALLS>(a, st);   // TMA-staged rows
+        // TMA-staged rows: two rows per iteration and six stages, or one row and four
+        if (cfg.vec == 7 && tma_ok(a, UK)) return launch_tma_d2q9<STORE, UK, WALLS, 2, 6>(a, st);
+        if (cfg.vec == 8 && tma_ok(a, UK)) return launch_tma_d2q9<STORE, UK, WALLS, 1, 4>(a, st);
         if (cfg.vec == 5 && a.nz == 1 && pair_ok(a, UK, L::Q)) {
             // node-pair variant (paired FP32 arithmetic, two adjacent nodes per thread)
             const int per = 2 * cfg.block;

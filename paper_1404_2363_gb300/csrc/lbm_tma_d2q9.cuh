@@ -23,17 +23,15 @@
 
 namespace lbm {
 
-#ifndef LBM_TMA_ROWS
-#define LBM_TMA_ROWS 2
-#endif
-#ifndef LBM_TMA_STAGES
-#define LBM_TMA_STAGES (2 * LBM_TMA_ROWS + 2)
-#endif
-constexpr int TMA_W = 256;                 // strip width in nodes (one box per plane row)
-constexpr int TMA_R = LBM_TMA_ROWS;        // grid rows computed per iteration
-constexpr int TMA_T = 128 * TMA_R;         // threads per CTA: 128 node pairs per row
-constexpr int TMA_NS = LBM_TMA_STAGES;     // ring stages (grid rows): R + 2 in use, the rest in flight
-static_assert(TMA_NS >= TMA_R + 2, "the ring must hold the R + 2 rows one iteration reads");
+constexpr int TMA_W = 256;    // strip width in nodes (one box per plane row)
+// Per instantiation: R grid rows computed per iteration by 128 R threads (128
+// node pairs per row) and a ring of NS >= R + 2 stages (R + 2 rows in use, the
+// rest in flight). Launch vec 7: R = 2, NS = 6; vec 8: R = 1, NS = 4.
+template <int R, int NS>
+struct TmaShape {
+    static_assert(NS >= R + 2, "the ring must hold the R + 2 rows one iteration reads");
+    static constexpr int threads = 128 * R;
+};
 // stage layout in bytes; every copy destination is 128-byte aligned
 constexpr int TS_G = 0;                       // [9][256] offsets
 constexpr int TS_GL = TS_G + 9 * TMA_W * 2;   // [9][8] columns xs - 8 .. xs - 1
@@ -45,7 +43,7 @@ constexpr int TS_U = TS_PR + 128;             // [2][256] velocity factors
 constexpr int TS_UL = TS_U + 2 * TMA_W * 4;   // [2][4]
 constexpr int TS_UR = TS_UL + 128;            // [2][4]
 constexpr int TS_BYTES = TS_UR + 128;         // 8704 bytes per stage
-constexpr int TMA_SMEM = TMA_NS * TS_BYTES + TMA_NS * 8;   // + one mbarrier per stage
+constexpr int tma_smem(int ns) { return ns * TS_BYTES + ns * 8; }   // + one mbarrier per stage
 constexpr long long TMA_DRAIN_LIMIT = 4000000000LL;         // clock64 cycles (about 2 s)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
@@ -121,8 +119,9 @@ __device__ __forceinline__ void stage_window(const unsigned char* st, int off, i
     w[2] = make_float2(c.y, r);
 }
 
-template <int STORE, int UK, bool WALLS>
-__global__ void __launch_bounds__(TMA_T) k_step_tma_d2q9(const StepArgs a, const __grid_constant__ TmaMaps m)
+template <int STORE, int UK, bool WALLS, int TMA_R, int TMA_NS>
+__global__ void __launch_bounds__(TmaShape<TMA_R, TMA_NS>::threads)
+    k_step_tma_d2q9(const StepArgs a, const __grid_constant__ TmaMaps m)
 {
     using P = Pair<STORE>;
     using T2 = typename P::T2;
@@ -310,22 +309,27 @@ __global__ void __launch_bounds__(TMA_T) k_step_tma_d2q9(const StepArgs a, const
 
 // One wave of CTAs: strips x block rows, with as many block rows as the
 // resident CTAs (per SM x SMs) allow per strip.
-template <int STORE, int UK, bool WALLS>
+template <int STORE, int UK, bool WALLS, int R, int NS>
 cudaError_t launch_tma_d2q9(const StepArgs& a, cudaStream_t st)
 {
-    static int resident = 0;   // per instantiation
+    constexpr int threads = TmaShape<R, NS>::threads, smem = tma_smem(NS);
+    static int resident_by_dev[64] = {0};   // per instantiation and device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int& resident = resident_by_dev[dev & 63];
     if (resident == 0) {
-        int dev = 0, nsm = 0, per_sm = 0;
-        cudaGetDevice(&dev);
+        int nsm = 0, per_sm = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_step_tma_d2q9<STORE, UK, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_tma_d2q9<STORE, UK, WALLS>, TMA_T, TMA_SMEM);
+        cudaFuncSetAttribute(k_step_tma_d2q9<STORE, UK, WALLS, R, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_tma_d2q9<STORE, UK, WALLS, R, NS>, threads,
+                                                      smem);
         resident = (nsm > 0 ? nsm : 1) * (per_sm > 0 ? per_sm : 1);
     }
     const int nstrip = a.nx / TMA_W;
     int nb = resident / nstrip;
     nb = nb < 1 ? 1 : (nb > a.ny ? a.ny : nb);
-    k_step_tma_d2q9<STORE, UK, WALLS><<<dim3((unsigned)nstrip, (unsigned)nb), TMA_T, TMA_SMEM, st>>>(a, *a.tma);
+    k_step_tma_d2q9<STORE, UK, WALLS, R, NS><<<dim3((unsigned)nstrip, (unsigned)nb), threads, smem, st>>>(a, *a.tma);
     return cudaGetLastError();
 }
 

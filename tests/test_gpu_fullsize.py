@@ -18,10 +18,10 @@ pytestmark = pytest.mark.gpu
                                                ("f16", 2e-3, (128, 5)), ("bf16", 2e-3, (128, 5)),
                                                ("f16", 2e-3, (64, 6)), ("bf16", 2e-3, (128, 6)),
                                                ("f32", 1e-5, (128, 6)), ("f16", 2e-3, (128, 7)),
-                                               ("bf16", 2e-3, (128, 7))])
+                                               ("bf16", 2e-3, (128, 7)), ("f16", 2e-3, (128, 8))])
 def test_vortex_4096_windows(O, storage, tol, launch):
-    """launch (., 5) / (., 6) / (128, 7): the node-pair, node-quad and TMA-staged
-    kernels; bench.py times the autotuner's choice among them."""
+    """launch (., 5) / (., 6) / (128, 7 or 8): the node-pair, node-quad and
+    TMA-staged kernels; bench.py times the autotuner's choice among them."""
     N, tau, nsteps, half = 4096, 1.0, 24, 40
     wl = W.vortex_workload(N, tau)
     s = Solver(nx=N, ny=N, storage=storage)
@@ -116,7 +116,8 @@ def test_d3q15_1000_steps_error_vs_fp64(O, storage, launch):
 @pytest.mark.parametrize("storage,tol,launch", [("f32", 1e-5, None), ("f16", 2e-3, None), ("bf16", 2e-3, None),
                                                ("f16", 2e-3, (64, 5)), ("bf16", 2e-3, (64, 5)),
                                                ("f16", 2e-3, (64, 6)), ("bf16", 2e-3, (64, 6)),
-                                               ("f16", 2e-3, (128, 7)), ("bf16", 2e-3, (128, 7))])
+                                               ("f16", 2e-3, (128, 7)), ("bf16", 2e-3, (128, 7)),
+                                               ("f16", 2e-3, (128, 8))])
 def test_vortex_5000_steps_error_vs_fp64(O, storage, tol, launch):
     """The configured length of the time-varying-velocity workload (5000 steps,
     tau = 1, full anisotropic D, Gaussian hill, vortex u(x, t)) on a 256^2 grid that

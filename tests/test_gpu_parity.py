@@ -184,19 +184,20 @@ def test_quad_kernel_narrow_grids(O, nx, ny):
         assert rel_l2(got, want) <= TOL[storage], (storage, nx, ny)
 
 
+@pytest.mark.parametrize("vec", [7, 8])
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 @pytest.mark.parametrize("bc,ukind", [(("periodic", "periodic"), "field"), (("noflux", "noflux"), "row"),
                                       (("bounceback", "bounceback"), "field"),
                                       (("dirichlet", "dirichlet"), "field"), (("periodic", "periodic"), "none")])
-def test_tma_offset_kernel(O, storage, bc, ukind):
-    """The TMA-staged kernel of the D2Q9 16-bit forms (launch vec = 7: source rows
-    staged in shared memory by tensor copies, persistent CTAs) against the oracle
-    on a 512 x 37 grid (74 strip rows: one-row work ranges), and against the
-    node-pair kernel, whose arithmetic it shares."""
+def test_tma_offset_kernel(O, storage, bc, ukind, vec):
+    """The TMA-staged kernel of the D2Q9 16-bit forms (launch vec 7 / 8: source
+    rows staged in shared memory by tensor copies, two or one rows per iteration)
+    against the oracle on a 512 x 37 grid (74 strip rows: one-row work ranges), and
+    against the node-pair kernel, whose arithmetic it shares."""
     case = Case(storage=storage, bc=bc, ukind=ukind, sched=ukind != "none", nx=512, ny=37,
                 phi_w=(1.0, 0.25) if bc[0] == "dirichlet" else (0.0, 0.0))
     phi0, a, sched = case.inputs()
-    got, s = _run_vec3(case, phi0, a, sched, vec=7, block=128)
+    got, s = _run_vec3(case, phi0, a, sched, vec=vec, block=128)
     s.sync()
     want = run_oracle(O, case, phi0, a, sched)
     assert rel_l2(got, want) <= TOL[storage]
@@ -206,16 +207,15 @@ def test_tma_offset_kernel(O, storage, bc, ukind):
 
 @pytest.mark.parametrize("nx,ny,steps", [(768, 600, 12), (256, 1, 30), (256, 3, 30), (1024, 5, 20)])
 def test_tma_kernel_work_ranges(O, nx, ny, steps):
-    """Work ranges that cross strip boundaries (768 x 600: three strips, about
-    three strip rows per CTA), a one-row and a three-row periodic grid (every
-    staged row wraps), and four strips of five rows."""
-    for storage in ("f16", "bf16"):
+    """Row ranges of odd and even lengths (768 x 600: three strips), a one-row and
+    a three-row periodic grid (every staged row wraps), four strips of five rows."""
+    for storage, vec in (("f16", 7), ("bf16", 7), ("bf16", 8)):
         case = Case(storage=storage, nx=nx, ny=ny, steps=steps)
         phi0, a, sched = case.inputs()
-        got, s = _run_vec3(case, phi0, a, sched, vec=7, block=128)
+        got, s = _run_vec3(case, phi0, a, sched, vec=vec, block=128)
         s.sync()
         want = run_oracle(O, case, phi0, a, sched)
-        assert rel_l2(got, want) <= TOL[storage], (storage, nx, ny)
+        assert rel_l2(got, want) <= TOL[storage], (storage, vec, nx, ny)
 
 
 def test_tma_wait_timeout_is_reported_and_handle_recovers(O):
