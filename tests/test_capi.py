@@ -50,3 +50,6 @@ def test_mixed_periodic_walls_rejected(L):
 def test_null_handle_calls(L):
     assert L.lbm_cde_step(None, 1) == N.LBM_E_ARG
     assert L.lbm_cde_destroy(None) == N.LBM_OK
+    assert L.lbm_cde_set_wait_limit(None, 100) == N.LBM_E_ARG
+    assert L.lbm_cde_set_launch(None, 128, 7) == N.LBM_E_ARG
+    assert L.lbm_cde_sync(None) == N.LBM_E_ARG
