@@ -57,3 +57,24 @@ def test_reference_arm_nonzero_rank_exits_quietly():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
                         "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_profile_traffic_only_for_the_profiled_sources(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu summary only while its
+    source_sha matches the current kernel sources; otherwise it is null."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    h = bench.kernel_source_hash()
+    good = tmp_path / "good.md"
+    good.write_text(f"source_sha = {h}\ntraffic_bytes_per_launch[f32] = 1.25e9\n")
+    monkeypatch.setattr(bench, "PROFILE", str(good))
+    assert bench.profile_traffic("f32") == 1.25e9
+    assert bench.profile_traffic("bf16") is None
+    stale = tmp_path / "stale.md"
+    stale.write_text("source_sha = 0123456789abcdef\ntraffic_bytes_per_launch[f32] = 1.25e9\n")
+    monkeypatch.setattr(bench, "PROFILE", str(stale))
+    assert bench.profile_traffic("f32") is None
+    # the committed summary matches the committed sources
+    monkeypatch.undo()
+    assert bench.profile_traffic("f32") is not None
