@@ -1,6 +1,6 @@
 // Tensor maps for the TMA-staged D2Q9 step (host side). The encoder comes from
-// the driver through the runtime's entry-point query, so the library does not
-// link the driver API.
+// the CUDA driver through the runtime's entry-point query, so the library does
+// not link libcuda.
 #include <cudaTypedefs.h>
 
 #include "lbm_internal.cuh"
