@@ -289,6 +289,18 @@ lbm_status lbm_cde_forward_ckpt(lbm_cde_t h, const float* phi0_dev, int64_t nste
 lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dphi0_dev, double* dL_dD_host,
                             double* dL_ds_host, float* dL_da_dev);
 
+/* Per-phase device timing of lbm_cde_backward (measurement aid, not in the
+ * paper). With on != 0 every later backward sweep records CUDA events on the
+ * handle's stream around each checkpoint segment's recompute and reverse steps;
+ * lbm_cde_backward_phases then returns, for the last sweep, ms_out[0] = the
+ * recompute time, ms_out[1] = the reverse steps with their gradient reductions,
+ * ms_out[2] = the whole sweep from its first to its last device operation
+ * (host array of 3 doubles; zeros before the first profiled sweep). The events
+ * add a little launch overhead, so profiled and unprofiled sweeps differ
+ * slightly. Errors: LBM_E_ARG (NULL argument). */
+lbm_status lbm_cde_set_profiling(lbm_cde_t h, int32_t on);
+lbm_status lbm_cde_backward_phases(lbm_cde_t h, double* ms_out);
+
 /* ---- Batched channels (Sec. 3.2 set-up, many instances per launch) --------
  * Independent D2Q9 MRT-A instances of uneven size, each with its own D, rates,
  * walls and row velocity profile u(y), advanced together; every step also
@@ -382,7 +394,10 @@ const char* lbm_cde_batch_last_error(lbm_cde_batch_t b);
  *   stream    : cudaStream_t (NULL: legacy stream); asynchronous
  * The first call on a device resolves the array's device address with
  * cudaGetSymbolAddress (with that device current); make that first call before
- * capturing a stream into a graph. Every call overwrites the partials it uses,
+ * capturing a stream into a graph. That address is kept for the life of the
+ * process: calls made after cudaDeviceReset (or any other teardown of the
+ * device's primary context) in the same process are not supported, since the
+ * array then lives at a new address. Every call overwrites the partials it uses,
  * so nothing needs clearing, but all calls on a GPU share the one array: calls
  * whose kernels overlap on the GPU (unordered streams) race. Errors: LBM_E_ARG,
  * LBM_E_CUDA; lbm_cde_noalloc_last_error() describes the last failure of the

@@ -121,6 +121,8 @@ SIGNATURES = {
     "lbm_cde_grad_rates": [_P, _DP, _DP, _DP],
     "lbm_cde_forward_ckpt": [_P, _P, _I64, _I64, _P],
     "lbm_cde_backward": [_P, _P, _P, _DP, _DP, _P],
+    "lbm_cde_set_profiling": [_P, ctypes.c_int32],
+    "lbm_cde_backward_phases": [_P, _DP],
     "lbm_cde_batch_opts_init": [ctypes.POINTER(BatchOpts)],
     "lbm_cde_batch_create": [ctypes.POINTER(ChannelDesc), ctypes.c_int32, ctypes.POINTER(BatchOpts),
                              ctypes.POINTER(_P)],

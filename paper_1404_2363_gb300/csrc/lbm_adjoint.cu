@@ -50,27 +50,33 @@ __device__ __forceinline__ void csum_merge(float2& acc, float2 o)
 // Rows handled by one block of the adjoint kernel (AdjArgs::rows): the gradient
 // partials of that many nodes per thread are summed in registers before the
 // block reduction. At most ADJ_ROWS; fewer on small grids, so that the grid
-// still fills the GPU (adjoint_rows).
+// still fills the GPU several times over. (A grid of exactly one resident wave,
+// each block walking rows gridDim.y apart, measured slower: 2.99x instead of
+// 2.55x a forward step at 4096^2.)
 constexpr int ADJ_ROWS = 8;
 
-int adjoint_rows(long long nx, long long ny, long long nz)
+int adjoint_rows(long long nx, long long ny, long long nz, int sms)
 {
     int rows = ADJ_ROWS;
-    while (rows > 1 && ((nx + 255) / 256) * ((ny + rows - 1) / rows) * nz < 152LL * 8) rows /= 2;
+    while (rows > 1 && ((nx + 255) / 256) * ((ny + rows - 1) / rows) * nz < (long long)sms * 8) rows /= 2;
     return rows;
 }
 
 // DA: the velocity-field gradient is accumulated (UK == U_FIELD only); its
 // running values are requested with the other loads of the node, and the
 // instance runs at 3 blocks per SM (80 registers) to hold them.
-template <class L, int UK, bool WALLS, bool DA>
+// IX: int when every plane offset fits in 31 bits (fewer address
+// instructions), long long otherwise. The maps M f, M mu and M^T c use the
+// same sums and differences of same-speed populations as the forward step
+// (moments / populations): the kernel is bound by its instruction issue.
+template <class L, int UK, bool WALLS, bool DA, typename IX>
 __global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(const AdjArgs a)
 {
     constexpr int Q = L::Q, DIM = L::DIM, NG = ngrad<L>();
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int z = blockIdx.z;
-    const long long N = a.ncell;
+    const IX N = (IX)a.ncell;
     const bool live = x < nx;
     const int xc = live ? x : nx - 1;
     const int xs[3] = {xc + 1 == nx ? 0 : xc + 1, xc, xc == 0 ? nx - 1 : xc - 1};
@@ -87,22 +93,26 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(con
 #pragma unroll 1
     for (int y = y0; y < y0 + a.rows && y < ny; ++y) {
         const int ys[3] = {y + 1 == ny ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};
-        const long long cell = (long long)xc + (long long)nx * (y + (long long)ny * z);
-        // pull source of population i = push target of its adjoint (recomputed
-        // where used rather than held in 64-bit registers through the step)
-        auto tgt = [&](int i) -> long long {
-            return (long long)xs[L::ex(i) + 1] + (long long)nx * (ys[L::ey(i) + 1] + (long long)ny * zs[L::ez(i) + 1]);
-        };
+        // row offsets of the source rows (y - e_y, z - e_z)
+        IX roff[3][3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                roff[b][d] = DIM == 2 ? (IX)nx * (IX)ys[b] : (IX)nx * ((IX)ys[b] + (IX)ny * (IX)zs[d]);
+        const IX cell = (IX)xc + roff[1][1];
+        // pull source of population i = push target of its adjoint
+        auto tgt = [&](int i) -> IX { return (IX)xs[L::ex(i) + 1] + roff[L::ey(i) + 1][L::ez(i) + 1]; };
         float mu[Q], f[Q];
         float du_old[DIM];
         if (DA && live) {
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) du_old[d] = a.du_acc[(long long)d * N + cell];
+            for (int d = 0; d < DIM; ++d) du_old[d] = a.du_acc[(IX)d * N + cell];
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            mu[i] = __ldg(a.mu_in + (long long)i * N + cell);
-            f[i] = __ldg(a.fprev + (long long)i * N + tgt(i));
+            mu[i] = __ldg(a.mu_in + (IX)i * N + cell);
+            f[i] = __ldg(a.fprev + (IX)i * N + tgt(i));
         }
         const bool lo = WALLS && y == 0 && a.bc_lo != BC_PERIODIC;
         const bool hi = WALLS && y == ny - 1 && a.bc_hi != BC_PERIODIC;
@@ -112,17 +122,24 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(con
             for (int i = 0; i < Q; ++i)
                 if (L::ey(i) != 0 && ((L::ey(i) == 1) == lo)) {
                     if (kind == BC_NOFLUX) f[i] = f[mirror_y<L>(i)];
-                    else f[i] = __ldg(a.fprev + (long long)opposite<L>(i) * N + cell);
+                    else f[i] = __ldg(a.fprev + (IX)opposite<L>(i) * N + cell);
                 }
         }
-        float ux, uy, uz;
-        vel_at_p<UK, DIM>(a.ua, a.ncell, a.ny, cell, y, s_now, ux, uy, uz);
+        float ux = 0.f, uy = 0.f, uz = 0.f;
+        if (UK == U_FIELD) {
+            ux = __fmul_rn(__ldg(a.ua + cell), s_now[0]);
+            uy = __fmul_rn(__ldg(a.ua + N + cell), s_now[1]);
+            if (DIM == 3) uz = __fmul_rn(__ldg(a.ua + 2 * N + cell), s_now[2]);
+        } else if (UK == U_ROW) {
+            ux = __fmul_rn(__ldg(a.ua + y), s_now[0]);
+            uy = __fmul_rn(__ldg(a.ua + ny + y), s_now[1]);
+            if (DIM == 3) uz = __fmul_rn(__ldg(a.ua + 2 * ny + y), s_now[2]);
+        }
         const float u[3] = {ux, uy, uz};
 
         // forward non-equilibrium moments d = M f - m^eq(phi, u(k))
         float m[Q];
-#pragma unroll
-        for (int k = 0; k < Q; ++k) m[k] = int_dot<Q>([k](int i) { return L::M(k, i); }, f);
+        moments<L>(f, m);
         const float phi = m[0];
         float v[Q];
 #pragma unroll
@@ -137,13 +154,12 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(con
         }
         float dm[Q];
 #pragma unroll
-        for (int k = 0; k < Q; ++k) dm[k] = m[k] - phi * v[k];
+        for (int k = 1; k < Q; ++k) dm[k] = fmaf(-phi, v[k], m[k]);
         dm[0] = 0.f;
 
         // a = M^-T mu = diag(1/|M_r|^2) M mu
         float av[Q];
-#pragma unroll
-        for (int k = 0; k < Q; ++k) av[k] = int_dot<Q>([k](int i) { return L::M(k, i); }, mu);
+        moments<L>(mu, av);
 #pragma unroll
         for (int k = 0; k < Q; ++k) av[k] *= 1.0f / (float)row_norm2<L>(k);
         // b = S^T a (S of Eq. 31 / A.5: diagonal rates, flux block A, couplings C)
@@ -169,21 +185,20 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(con
         for (int k = 0; k < Q; ++k) cv[k] = av[k] - b[k];
         cv[0] += vb;
         float nu[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) nu[i] = int_dot<Q>([i](int k) { return L::M(k, i); }, cv);
+        populations<L, false, true>(cv, nu);   // nu = M^T c
         if (!live) continue;
 
         // velocity partials: u(x, k) = a(x) s(k)  =>  dL/da += s(k) dL/du(k)
         if (DA) {
 #pragma unroll
             for (int d = 0; d < DIM; ++d)
-                a.du_acc[(long long)d * N + cell] = du_old[d] + phi * (b[3 + 2 * d] - b[4 + 2 * d]) * s_now[d];
+                a.du_acc[(IX)d * N + cell] = du_old[d] + phi * (b[3 + 2 * d] - b[4 + 2 * d]) * s_now[d];
         } else if (UK == U_FIELD && a.du_acc != nullptr) {
             // never taken (gradient buffers go to the DA instance); kept because this
             // instance measured faster with it (register allocation)
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
-                float* p = a.du_acc + (long long)d * N + cell;
+                float* p = a.du_acc + (IX)d * N + cell;
                 *p += phi * (b[3 + 2 * d] - b[4 + 2 * d]) * s_now[d];
             }
         }
@@ -205,18 +220,18 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(con
             for (int i = 0; i < Q; ++i) {
                 if (L::ey(i) != 0 && ((L::ey(i) == 1) == lo)) {          // entered from beyond the wall
                     if (kind == BC_NOFLUX) nu[mirror_y<L>(i)] += nu[i];
-                    else out[(long long)opposite<L>(i) * N + cell] = nu[i];
+                    else out[(IX)opposite<L>(i) * N + cell] = nu[i];
                 }
             }
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 if (L::ey(i) != 0 && ((L::ey(i) == 1) == lo)) continue;
-                if (kind == BC_NOFLUX && L::ey(i) != 0) out[(long long)i * N + cell] = 0.f;  // left the domain
-                out[(long long)i * N + tgt(i)] = nu[i];
+                if (kind == BC_NOFLUX && L::ey(i) != 0) out[(IX)i * N + cell] = 0.f;  // left the domain
+                out[(IX)i * N + tgt(i)] = nu[i];
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) out[(long long)i * N + tgt(i)] = nu[i];
+            for (int i = 0; i < Q; ++i) out[(IX)i * N + tgt(i)] = nu[i];
         }
     }
 
@@ -240,14 +255,15 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(con
     }
 }
 
-// Deterministic two-level sum of the per-block partials ([nslice][NG][nblocks],
-// one slice per reverse step since the last reduction): pass 2 reduces
+// Deterministic two-level sum of the per-block partials ([NG][nblocks] in each
+// of nslice slices `slice` floats apart, one slice per reverse step since the
+// last reduction): pass 2 reduces
 // GRAD_CHUNKS contiguous chunks of every row of every slice in parallel, pass 3
 // adds the chunk sums in index order to the running totals.
 constexpr int GRAD_CHUNKS = 32;
 
 __global__ void __launch_bounds__(256) k_grad_sum2(const float* __restrict__ partials, long long nblocks,
-                                                   int ng, int nslice, float2* __restrict__ p2)
+                                                   long long slice, int ng, int nslice, float2* __restrict__ p2)
 {
     const int r = blockIdx.x, j = blockIdx.y;
     const long long len = (nblocks + GRAD_CHUNKS - 1) / GRAD_CHUNKS;
@@ -255,7 +271,7 @@ __global__ void __launch_bounds__(256) k_grad_sum2(const float* __restrict__ par
     const long long b1 = b0 + len < nblocks ? b0 + len : nblocks;
     float2 s = make_float2(0.f, 0.f);
     for (int sl = 0; sl < nslice; ++sl) {
-        const float* row = partials + ((long long)sl * ng + j) * nblocks;
+        const float* row = partials + (long long)sl * slice + (long long)j * nblocks;
         for (long long b = b0 + threadIdx.x; b < b1; b += blockDim.x) csum_add(s, row[b]);
     }
     __shared__ float2 red[256];
@@ -324,37 +340,44 @@ static long long adj_blocks(const AdjArgs& a)
 
 // grad_acc += the per-block partials of nslice slices starting at base, summed in a fixed order
 template <class L>
-static cudaError_t grad_reduce(const AdjArgs& a, float* base, int nslice, cudaStream_t st)
+static cudaError_t grad_reduce(const AdjArgs& a, float* base, int nslice, long long slice, cudaStream_t st)
 {
     constexpr int NG = ngrad<L>();
     const long long nb = adj_blocks(a);
-    const long long off = ((long long)ADJ_SLICES * nb * NG + 1) & ~1LL;   // 8-byte aligned chunk sums
-    float2* p2 = reinterpret_cast<float2*>(base + off);
-    k_grad_sum2<<<dim3(GRAD_CHUNKS, NG), 256, 0, st>>>(base, nb, NG, nslice, p2);
+    float2* p2 = reinterpret_cast<float2*>(base + (long long)ADJ_SLICES * slice);   // slice is even
+    k_grad_sum2<<<dim3(GRAD_CHUNKS, NG), 256, 0, st>>>(base, nb, slice, NG, nslice, p2);
     k_grad_sum3<<<1, 64, 0, st>>>(p2, NG, a.grad_acc);
     return cudaGetLastError();
+}
+
+template <class L, int UK, typename IX>
+static cudaError_t adj_ix(bool walls, const AdjArgs& a, cudaStream_t st, bool reduce)
+{
+    dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)((a.ny + a.rows - 1) / a.rows), (unsigned)a.nz);
+    if constexpr (UK == U_FIELD) {
+        if (a.du_acc != nullptr) {
+            if (walls) k_adjoint<L, UK, true, true, IX><<<grid, 256, 0, st>>>(a);
+            else k_adjoint<L, UK, false, true, IX><<<grid, 256, 0, st>>>(a);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess || !reduce) return e;
+            return grad_reduce<L>(a, a.partials, 1, 0, st);
+        }
+    }
+    {
+        if (walls) k_adjoint<L, UK, true, false, IX><<<grid, 256, 0, st>>>(a);
+        else k_adjoint<L, UK, false, false, IX><<<grid, 256, 0, st>>>(a);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !reduce) return e;
+    return grad_reduce<L>(a, a.partials, 1, 0, st);
 }
 
 template <class L, int UK>
 static cudaError_t adj_w(bool walls, const AdjArgs& a, cudaStream_t st, bool reduce)
 {
-    dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)((a.ny + a.rows - 1) / a.rows), (unsigned)a.nz);
-    if constexpr (UK == U_FIELD) {
-        if (a.du_acc != nullptr) {
-            if (walls) k_adjoint<L, UK, true, true><<<grid, 256, 0, st>>>(a);
-            else k_adjoint<L, UK, false, true><<<grid, 256, 0, st>>>(a);
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess || !reduce) return e;
-            return grad_reduce<L>(a, a.partials, 1, st);
-        }
-    }
-    {
-        if (walls) k_adjoint<L, UK, true, false><<<grid, 256, 0, st>>>(a);
-        else k_adjoint<L, UK, false, false><<<grid, 256, 0, st>>>(a);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !reduce) return e;
-    return grad_reduce<L>(a, a.partials, 1, st);
+    // 32-bit offsets when every plane (and the velocity planes) fits
+    if ((long long)(L::Q + L::DIM) * a.ncell < (1LL << 31)) return adj_ix<L, UK, int>(walls, a, st, reduce);
+    return adj_ix<L, UK, long long>(walls, a, st, reduce);
 }
 
 template <class L>
@@ -372,23 +395,26 @@ cudaError_t launch_adjoint(int q, int ukind, bool walls, const AdjArgs& a, cudaS
     return q == 9 ? adj_u<D2Q9>(ukind, walls, a, st, reduce) : adj_u<D3Q15>(ukind, walls, a, st, reduce);
 }
 
-cudaError_t launch_grad_reduce(int q, const AdjArgs& a, float* base, int nslice, cudaStream_t st)
+cudaError_t launch_grad_reduce(int q, const AdjArgs& a, float* base, int nslice, long long slice, cudaStream_t st)
 {
-    return q == 9 ? grad_reduce<D2Q9>(a, base, nslice, st) : grad_reduce<D3Q15>(a, base, nslice, st);
+    return q == 9 ? grad_reduce<D2Q9>(a, base, nslice, slice, st) : grad_reduce<D3Q15>(a, base, nslice, slice, st);
 }
 
-long long adjoint_slice_size(int q, long long nx, long long ny, long long nz)
+// Floats of one slice of block partials ([NG][nblocks]), rounded up to an even
+// count (8-byte aligned slices).
+long long adjoint_slice_size(int q, long long nx, long long ny, long long nz, int sms)
 {
-    const int rows = adjoint_rows(nx, ny, nz);
-    return ((nx + 255) / 256) * ((ny + rows - 1) / rows) * nz * (q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>());
-}
-
-long long adjoint_partials_size(int q, long long nx, long long ny, long long nz)
-{
-    const int rows = adjoint_rows(nx, ny, nz);
+    const int rows = adjoint_rows(nx, ny, nz, sms);
     const long long nb = ((nx + 255) / 256) * ((ny + rows - 1) / rows) * nz;
-    // ADJ_SLICES slices of [NG][nb] floats, then the [NG][GRAD_CHUNKS] float2 chunk sums
-    return (ADJ_SLICES * nb + 2 * GRAD_CHUNKS) * (q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>()) + 2;
+    const long long f = nb * (q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>());
+    return (f + 1) & ~1LL;
+}
+
+long long adjoint_partials_size(int q, long long nx, long long ny, long long nz, int sms)
+{
+    // ADJ_SLICES slices, then the [NG][GRAD_CHUNKS] float2 chunk sums
+    return ADJ_SLICES * adjoint_slice_size(q, nx, ny, nz, sms) +
+           2LL * GRAD_CHUNKS * (q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>());
 }
 
 int adjoint_ngrad(int q) { return q == 9 ? ngrad<D2Q9>() : ngrad<D3Q15>(); }

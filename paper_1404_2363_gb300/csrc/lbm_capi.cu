@@ -60,6 +60,10 @@ struct lbm_cde_s {
     const float* tmaps_ua = nullptr;
     int* status_dev = nullptr;
     long long wait_limit = 4000000000LL;   // SM cycles per bounded device wait (about 2 s)
+    int sms = 152;                         // multiprocessors of the device (adjoint grid)
+    // per-phase device time of the last backward sweep (lbm_cde_set_profiling)
+    bool prof = false;
+    double prof_ms[3] = {0, 0, 0};
 };
 
 static thread_local std::string g_create_err;
@@ -377,6 +381,13 @@ lbm_status lbm_cde_create(const lbm_cde_desc* desc, lbm_cde_t* out)
     if (!h->status_dev || cudaMemsetAsync(h->status_dev, 0, 16, h->st) != cudaSuccess) {
         lbm_cde_destroy(h);
         return fail(nullptr, LBM_E_OOM, "status word allocation failed");
+    }
+    {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+            h->sms = n;
+        cudaGetLastError();
     }
     // launch shape: 256 threads along x, cells per thread chosen for the row length
     h->cfg.block = d.nx >= 256 ? 256 : (d.nx >= 128 ? 128 : 64);
@@ -767,7 +778,7 @@ static lbm_status ensure_adjoint_buffers(lbm_cde_t h)
             if (!h->mu[b]) return fail(h, LBM_E_OOM, "adjoint state allocation failed");
         }
     if (!h->adj_partials) {
-        const long long np = lbm::adjoint_partials_size(h->q, h->d.nx, h->d.ny, h->d.nz);
+        const long long np = lbm::adjoint_partials_size(h->q, h->d.nx, h->d.ny, h->d.nz, h->sms);
         const int ng = lbm::adjoint_ngrad(h->q);
         h->adj_partials = static_cast<float*>(dev_alloc(h, sizeof(float) * (np + 2 * ng)));
         if (!h->adj_partials) return fail(h, LBM_E_OOM, "adjoint scratch allocation failed");
@@ -788,7 +799,7 @@ static lbm::AdjArgs make_adj(lbm_cde_t h, int64_t k, const float* mu_in, float* 
     a.sched_len = h->sched_len;
     a.k = k;
     a.srow = lbm::sched_row(k, h->sched ? h->sched_len : 0);
-    a.rows = lbm::adjoint_rows(h->d.nx, h->d.ny, h->d.nz);
+    a.rows = lbm::adjoint_rows(h->d.nx, h->d.ny, h->d.nz, h->sms);
     a.nx = (int)h->d.nx;
     a.ny = (int)h->d.ny;
     a.nz = (int)h->d.nz;
@@ -933,8 +944,23 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
     const size_t sb = (size_t)h->ncell * 4 * h->q;
     const int uk = ukind_internal(h->ukind);
     const bool walls = h->d.bc_lo_y != LBM_BC_PERIODIC;
+    // optional per-phase timing: one event before and after each segment's recompute
+    // and after its reverse steps (lbm_cde_set_profiling)
+    struct Events {
+        std::vector<cudaEvent_t> e;
+        ~Events() { for (cudaEvent_t x : e) cudaEventDestroy(x); }
+        cudaError_t mark(cudaStream_t st)
+        {
+            cudaEvent_t x = nullptr;
+            cudaError_t r = cudaEventCreate(&x);
+            if (r != cudaSuccess) return r;
+            e.push_back(x);
+            return cudaEventRecord(x, st);
+        }
+    } ev;
+    if (h->prof) CK(h, ev.mark(h->st));
     CK(h, cudaMemsetAsync(h->grad_acc, 0, sizeof(float2) * ng, h->st));
-    const long long slice = lbm::adjoint_slice_size(h->q, h->d.nx, h->d.ny, h->d.nz);
+    const long long slice = lbm::adjoint_slice_size(h->q, h->d.nx, h->d.ny, h->d.nz, h->sms);
     int nslice = 0;   // reverse steps since the last gradient reduction
     if (dL_da_dev) CK(h, cudaMemsetAsync(dL_da_dev, 0, (size_t)h->ncell * 4 * h->dim, h->st));
     CK(h, lbm::launch_adjoint_seed(dL_dphiN_dev, h->mu[0], h->ncell, h->q, h->st));
@@ -948,6 +974,7 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
     for (int64_t j = nck - 1; j >= 0; --j) {
         const int64_t start = j * K;
         const int64_t end = std::min(start + K, Nst);
+        if (h->prof) CK(h, ev.mark(h->st));
         // recompute B_{start+1} .. B_{end-1} from the checkpoint
         for (int64_t t = 1; t < end - start; ++t) {
             StepArgs a = make_args(h, 0);
@@ -956,27 +983,61 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
             set_step(a, start + t);
             CK(h, lbm::launch_step(h->q, LBM_STORE_F32, uk, walls, h->cfg, a, h->st));
         }
+        if (h->prof) CK(h, ev.mark(h->st));
         for (int64_t k = end; k > start; --k) {
             lbm::AdjArgs a = make_adj(h, k, h->mu[cur], h->mu[1 - cur], seg_state(j, k - 1 - start), dL_da_dev,
                                       h->grad_acc);
             a.partials = h->adj_partials + nslice * slice;
             CK(h, lbm::launch_adjoint(h->q, uk, walls, a, h->st, false));
             if (++nslice == lbm::ADJ_SLICES) {
-                CK(h, lbm::launch_grad_reduce(h->q, a, h->adj_partials, nslice, h->st));
+                CK(h, lbm::launch_grad_reduce(h->q, a, h->adj_partials, nslice, slice, h->st));
                 nslice = 0;
             }
             cur ^= 1;
         }
+        if (h->prof) CK(h, ev.mark(h->st));
     }
     lbm::AdjArgs a0 = make_adj(h, 0, h->mu[cur], nullptr, nullptr, dL_da_dev, h->grad_acc);
-    if (nslice > 0) CK(h, lbm::launch_grad_reduce(h->q, a0, h->adj_partials, nslice, h->st));
+    if (nslice > 0) CK(h, lbm::launch_grad_reduce(h->q, a0, h->adj_partials, nslice, slice, h->st));
     CK(h, lbm::launch_adjoint_init(h->q, uk, a0, h->phi0_saved, dL_dphi0_dev, h->st));
     float2 gc[33];
     CK(h, cudaMemcpyAsync(gc, h->grad_acc, sizeof(float2) * ng, cudaMemcpyDeviceToHost, h->st));
+    if (h->prof) CK(h, ev.mark(h->st));
     CK(h, cudaStreamSynchronize(h->st));
+    if (h->prof) {
+        // events: start, then (before recompute, before reverse steps, after) per segment, end
+        double rec = 0.0, adj = 0.0, tot = 0.0;
+        float ms = 0.f;
+        const size_t ne = ev.e.size();
+        for (size_t j = 1; j + 2 < ne; j += 3) {
+            CK(h, cudaEventElapsedTime(&ms, ev.e[j], ev.e[j + 1]));
+            rec += ms;
+            CK(h, cudaEventElapsedTime(&ms, ev.e[j + 1], ev.e[j + 2]));
+            adj += ms;
+        }
+        CK(h, cudaEventElapsedTime(&ms, ev.e[0], ev.e[ne - 1]));
+        tot = ms;
+        h->prof_ms[0] = rec;
+        h->prof_ms[1] = adj;
+        h->prof_ms[2] = tot;
+    }
     double g[33];
     for (int j = 0; j < ng; ++j) g[j] = (double)gc[j].x + (double)gc[j].y;   // compensated sum, host FP64
     return lbm_cde_grad_rates(h, g, dL_dD_host, dL_ds_host);
+}
+
+lbm_status lbm_cde_set_profiling(lbm_cde_t h, int32_t on)
+{
+    if (!h) return fail(h, LBM_E_ARG, "NULL handle");
+    h->prof = on != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_cde_backward_phases(lbm_cde_t h, double* ms_out)
+{
+    if (!h || !ms_out) return fail(h, LBM_E_ARG, "NULL argument");
+    for (int j = 0; j < 3; ++j) ms_out[j] = h->prof_ms[j];
+    return LBM_OK;
 }
 
 const char* lbm_cde_last_error(lbm_cde_t h)

@@ -170,14 +170,14 @@ cudaError_t launch_sum(int q, int store, const StepArgs& a, double* partials, in
 // separate slices (AdjArgs::partials = base + slice * adjoint_slice_size) and
 // reduces them together with launch_grad_reduce.
 cudaError_t launch_adjoint(int q, int ukind, bool walls, const AdjArgs& a, cudaStream_t st, bool reduce);
-cudaError_t launch_grad_reduce(int q, const AdjArgs& a, float* base, int nslice, cudaStream_t st);
-long long adjoint_slice_size(int q, long long nx, long long ny, long long nz);
+cudaError_t launch_grad_reduce(int q, const AdjArgs& a, float* base, int nslice, long long slice, cudaStream_t st);
+long long adjoint_slice_size(int q, long long nx, long long ny, long long nz, int sms);
 constexpr int ADJ_SLICES = 16;   // reverse steps whose block partials are kept apart before one reduction
 cudaError_t launch_adjoint_init(int q, int ukind, const AdjArgs& a, const float* phi0, float* dphi0,
                                 cudaStream_t st);
 cudaError_t launch_adjoint_seed(const float* g, float* mu, long long ncell, int q, cudaStream_t st);
-long long adjoint_partials_size(int q, long long nx, long long ny, long long nz);   // in floats
-int adjoint_rows(long long nx, long long ny, long long nz);
+long long adjoint_partials_size(int q, long long nx, long long ny, long long nz, int sms);   // in floats
+int adjoint_rows(long long nx, long long ny, long long nz, int sms);
 int adjoint_ngrad(int q);
 
 }  // namespace lbm

@@ -81,7 +81,9 @@ __global__ void __launch_bounds__(kThreads) k_noalloc_sum2(const double* __restr
 
 // Device address of g_noalloc_partials, resolved once per device with that
 // device current. Host code must not pass the symbol itself to a kernel: on
-// the host it names a shadow variable, not device memory.
+// the host it names a shadow variable, not device memory. The cached address
+// belongs to the device's primary context of the moment; a device reset in
+// this process would move the array, and calls after one are unsupported.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {nullptr};

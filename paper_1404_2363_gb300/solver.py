@@ -211,6 +211,16 @@ class Solver:
                  "lbm_cde_backward")
         return dphi0, dD.reshape(self.dim, self.dim), ds, da
 
+    def set_profiling(self, on=True):
+        """Per-phase device timing of later backward() sweeps (backward_phases())."""
+        self._ck(self.L.lbm_cde_set_profiling(self.h, 1 if on else 0), "lbm_cde_set_profiling")
+
+    def backward_phases(self):
+        """(recompute ms, reverse steps ms, whole sweep ms) of the last profiled backward()."""
+        v = np.zeros(3)
+        self._ck(self.L.lbm_cde_backward_phases(self.h, v.ctypes.data_as(N._DP)), "lbm_cde_backward_phases")
+        return {"recompute_ms": float(v[0]), "reverse_steps_ms": float(v[1]), "sweep_ms": float(v[2])}
+
     def run_host(self, phi0: np.ndarray, nsteps: int, out: np.ndarray | None = None):
         phi0 = np.ascontiguousarray(phi0, dtype=np.float32)
         if out is None:

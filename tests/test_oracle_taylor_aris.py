@@ -12,13 +12,18 @@ converged limit with max(1 % relative, 5e-4 absolute).
 
 MRT-B1, B2 and B3 reproduce every checked entry within that tolerance, which
 pins M, the equilibria of Eq. 37-39, the unmodified S, the wall rule, the
-streaming and the estimator. MRT-A (modified S, Eq. 31) does not reproduce
-the printed MRT-A column with the printed relaxation rates: the paper's own
-ordering and its Pe-independence hold, but the level differs (about 1.3x at
-tau = 2, 2x at tau = 1, 0.96x at tau = 0.55). The modified S is pinned instead by
-its exact deviation-free variance growth (tests/test_oracle_step.py) and the
-hand-computed collisions (tests/test_oracle_collision.py); the discrepancy is
-recorded here as an observed bound.
+streaming and the estimator. MRT-A (modified S, Eq. 31) reproduces the printed
+MRT-A column's dependence on Pe at each tau (the ratio of our error to the
+printed one is the same for all four Pe of a table, to 0.2 %; a weak pin, since
+any error proportional to the Taylor part Pe^2 / 210 of alpha_L has that
+shape), but not its level: the ratio is 1.314 at tau = 2, 2.058 at tau = 1 and 0.961 at tau = 0.55.
+No single change of reading moves all three levels onto the printed ones
+(tests/golden/make_taylor_aris_mrt_a.py --study varies the free rates s1, s2,
+s7 = s8 and the cross-section weighting one at a time); the level is pinned
+instead by the exact deviation-free variance growth of the modified S
+(tests/test_oracle_step.py) and the hand-computed collisions
+(tests/test_oracle_collision.py), and here by the recorded oracle values
+(tests/golden/taylor_aris_mrt_a_oracle.txt, written by that script).
 """
 import math
 import os
@@ -51,7 +56,7 @@ def channel(O, tau, Pe, model, W=32):
     return p, ux, alpha
 
 
-def converged_er(O, tau, Pe, model, nsteps):
+def converged_er(O, tau, Pe, model, nsteps, signed=False):
     p, ux, alpha = channel(O, tau, Pe, model)
     ny = p.ny
     _, M, Mi, _ = O.tables(p)
@@ -65,7 +70,7 @@ def converged_er(O, tau, Pe, model, nsteps):
     # the limit has been reached: the last 1000 steps agree to 1e-7 (the
     # residual is FP64 cancellation in <x^2> - <x>^2, far below the tolerance)
     assert abs(a[-1] - a[-1000]) / a[-1] < 1e-7
-    return abs(a[-1] - an) / an * 100.0
+    return ((a[-1] - an) if signed else abs(a[-1] - an)) / an * 100.0
 
 
 def test_moment_recursion_equals_full_2d_oracle(O):
@@ -122,14 +127,43 @@ def test_b_models_reproduce_tables_3_to_5(O, tau, Pe):
     ours = [converged_er(O, tau, Pe, m, nsteps) for m in (O.MRT_A, O.MRT_B1, O.MRT_B2, O.MRT_B3)]
     for k in (1, 2, 3):
         assert abs(ours[k] - want[k]) <= max(0.01 * want[k], 5e-4), (k, ours[k], want[k])
-    # MRT-A: the paper's ordering against the B models holds (Sec. 3.2) ...
+    # MRT-A: the paper's ordering against the B models holds (Sec. 3.2)
     if tau >= 1.0:
         assert ours[0] < min(ours[1:])
     else:
         assert ours[0] < ours[3] < ours[1] < ours[2]
-    # ... and the level stays within the observed discrepancy band (reading note above)
-    ratio = ours[0] / want[0]
-    assert 0.9 < ratio < 2.2, ratio
+
+
+def recorded_mrt_a():
+    path = os.path.join(os.path.dirname(__file__), "golden", "taylor_aris_mrt_a_oracle.txt")
+    out = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        t, tau, Pe, signed, printed, ratio = line.split()
+        out[(float(tau), float(Pe))] = (float(signed), float(printed))
+    return out
+
+
+@pytest.mark.parametrize("tau", [2.0, 1.0, 0.55])
+def test_mrt_a_pe_dependence_matches_the_printed_column(O, tau):
+    """At fixed tau the oracle's MRT-A error is the printed MRT-A error times one
+    factor for every Pe of the table (0.5 %): the velocity dependence of the
+    modified model matches Tables 3-5; the factor itself is the recorded
+    discrepancy of the level, checked against the recorded oracle values (1 %)."""
+    table = {(r[1], r[2]): r[3] for r in load_tables()}
+    rec = recorded_mrt_a()
+    nsteps = 30000 if tau >= 1.0 else 200000
+    ratios = []
+    for (t, Pe), er in sorted(table.items()):
+        if t != tau:
+            continue
+        signed = converged_er(O, tau, Pe, O.MRT_A, nsteps, signed=True)
+        want_signed, printed = rec[(tau, Pe)]
+        assert abs(signed - want_signed) <= 0.01 * abs(want_signed), (tau, Pe, signed, want_signed)
+        ratios.append(abs(signed) / er[0])
+    assert len(ratios) == 4
+    assert max(ratios) / min(ratios) - 1.0 < 5e-3, ratios
 
 
 def test_error_ratio_nearly_independent_of_pe(O):
