@@ -9,7 +9,7 @@
  *
  * One time step (lbm_cde_step) is one fused CUDA kernel per cell:
  *   pull-stream f_i(x) <- f'_i(x - e_i)                  (Eq. 5, pull form)
- *   wall rules at the y = 0 / y = ny-1 nodes             (Sec. 3.2; see bc_*)
+ *   wall rules at the boundary nodes                      (Sec. 3.2; see bc_*)
  *   m = M f                                              (Eq. 11, 12 / A.2)
  *   m' = m - S (m - m^eq(phi, u))  with the modified S   (Eq. 13, 30-31 / A.5)
  *   f' = M^-1 m'                                         (Eq. 14)
@@ -17,8 +17,9 @@
  *
  * Conventions common to every entry point
  *   - Lattice units: dx = dt = c = 1.
- *   - Cell index c = x + nx * (y + ny * z); x (and z) are periodic, the two
- *     y faces take bc_lo_y / bc_hi_y.
+ *   - Cell index c = x + nx * (y + ny * z); every axis is periodic unless its
+ *     two faces carry walls (bc_lo_y / bc_hi_y, bc_lo_x / bc_hi_x, bc_lo_z /
+ *     bc_hi_z).
  *   - "dev" pointers are CUDA device pointers on the current device; "host"
  *     pointers are ordinary host memory (pinned memory is faster).
  *   - Per-cell arrays of vectors are SoA: u[a * ncell + c], a = 0 .. dim-1.
@@ -57,9 +58,13 @@ typedef enum {
 
 enum { LBM_D2Q9 = 9, LBM_D3Q15 = 15 };
 
-/* Wall kinds for the y faces. x (and z) are always periodic. */
+/* Wall kinds of the grid faces. The y faces take any kind; the x faces (and the
+ * z faces of D3Q15) take PERIODIC, NOFLUX_NODE or BOUNCEBACK. Where two wall
+ * faces meet, a population whose source lies beyond a bounce-back face returns
+ * reversed, and one whose source lies beyond Neumann faces copies the
+ * population reflected in the axes of those faces. */
 enum {
-    LBM_BC_PERIODIC = 0,    /* both y faces must then be periodic                   */
+    LBM_BC_PERIODIC = 0,    /* both faces of the axis must then be periodic         */
     LBM_BC_NOFLUX_NODE = 1, /* wall on the boundary node, Neumann d phi/dy = 0 by the
                                mirror rule of Sec. 3.2: at y = 0 f2=f4, f5=f8,
                                f6=f7; at y = ny-1 f4=f2, f7=f6, f8=f5 (D3Q15: every
@@ -120,6 +125,11 @@ typedef struct {
     void* stream;            /* cudaStream_t for every launch (NULL: legacy stream)  */
     int32_t model;           /* LBM_MRT_A (default) / LBM_MRT_B1 / B2 / B3; for the B
                                 models alpha1, alpha2 are fixed by their equilibria  */
+    int32_t bc_lo_x;         /* LBM_BC_PERIODIC / NOFLUX_NODE / BOUNCEBACK on x = 0;
+                                walls need nx >= 3                                   */
+    int32_t bc_hi_x;         /* the same on x = nx-1                                 */
+    int32_t bc_lo_z;         /* the same on z = 0 (D3Q15; walls need nz >= 3)        */
+    int32_t bc_hi_z;         /* the same on z = nz-1                                 */
 } lbm_cde_desc;
 
 /* Fills *d with defaults for a periodic grid (F32 storage, default alpha and

@@ -71,6 +71,10 @@ class _Params(ctypes.Structure):
         ("s", ctypes.c_double * 15),
         ("A", ctypes.c_double * 9),
         ("nthreads", ctypes.c_int32),
+        ("bcx_lo", ctypes.c_int32),
+        ("bcx_hi", ctypes.c_int32),
+        ("bcz_lo", ctypes.c_int32),
+        ("bcz_hi", ctypes.c_int32),
     ]
 
 
@@ -163,6 +167,10 @@ class Params:
     s: np.ndarray | None = None
     tie: bool = True
     nthreads: int = 0
+    bcx_lo: int = PERIODIC      # x faces: PERIODIC, NOFLUX_NODE or BOUNCEBACK
+    bcx_hi: int = PERIODIC
+    bcz_lo: int = PERIODIC      # z faces (D3Q15)
+    bcz_hi: int = PERIODIC
 
     @property
     def dim(self) -> int:
@@ -202,6 +210,8 @@ class Params:
         for k in range(9):
             p.A[k] = float(A[k]) if k < len(A) else 0.0
         p.nthreads = self.nthreads
+        p.bcx_lo, p.bcx_hi = self.bcx_lo, self.bcx_hi
+        p.bcz_lo, p.bcz_hi = self.bcz_lo, self.bcz_hi
         return p
 
 

@@ -32,9 +32,10 @@
 enum { ORC_MRT_A = 0, ORC_MRT_B1 = 1, ORC_MRT_B2 = 2, ORC_MRT_B3 = 3 };
 enum { ORC_PERIODIC = 0, ORC_NOFLUX_NODE = 1, ORC_BOUNCEBACK = 2, ORC_DIRICHLET = 3 };
 
-/* Parameters of one run.  x (and z) are periodic; the two y faces carry
- * bc_lo / bc_hi.  s[k] are the diagonal rates of S; the flux rows
- * (3, 5 in D2Q9; 3, 5, 7 in D3Q15) take the block A instead. */
+/* Parameters of one run.  The two y faces carry bc_lo / bc_hi (any wall kind);
+ * the x faces bcx_lo / bcx_hi and the z faces bcz_lo / bcz_hi (D3Q15) are
+ * periodic, NOFLUX_NODE or BOUNCEBACK.  s[k] are the diagonal rates of S; the
+ * flux rows (3, 5 in D2Q9; 3, 5, 7 in D3Q15) take the block A instead. */
 typedef struct {
     int32_t q;          /* 9 or 15 */
     int32_t model;      /* ORC_MRT_* (B models exist for D2Q9 only) */
@@ -45,6 +46,8 @@ typedef struct {
     double s[15];              /* diagonal relaxation rates s_0..s_{q-1} */
     double A[9];               /* flux block of S, row-major dim x dim */
     int32_t nthreads;          /* OpenMP threads (<= 0: library default) */
+    int32_t bcx_lo, bcx_hi;    /* x faces */
+    int32_t bcz_lo, bcz_hi;    /* z faces (D3Q15) */
 } orc_params;
 
 typedef struct {
@@ -197,6 +200,16 @@ static int build_lattice(orc_lattice* L, const orc_params* p)
     } else {
         return -1;
     }
+    /* x and z faces: both periodic or both walls, NOFLUX_NODE or BOUNCEBACK;
+     * D2Q9 has no z faces */
+    const int32_t fx[2] = {p->bcx_lo, p->bcx_hi}, fz[2] = {p->bcz_lo, p->bcz_hi};
+    for (int k = 0; k < 2; ++k) {
+        if (fx[k] < ORC_PERIODIC || fx[k] > ORC_BOUNCEBACK) return -5;
+        if (fz[k] < ORC_PERIODIC || fz[k] > ORC_BOUNCEBACK) return -5;
+    }
+    if ((fx[0] == ORC_PERIODIC) != (fx[1] == ORC_PERIODIC)) return -5;
+    if ((fz[0] == ORC_PERIODIC) != (fz[1] == ORC_PERIODIC)) return -5;
+    if (p->q == 9 && fz[0] != ORC_PERIODIC) return -5;
     if (invert(L->q, L->M, L->Minv) != 0) return -3;
     build_S(L, p);
     return 0;
@@ -337,6 +350,62 @@ static int opposite(const orc_lattice* L, int i)
     return -1;
 }
 
+/* Wall kind of face (axis a, side 0 = low / 1 = high). */
+static int face_kind(const orc_params* p, int a, int side)
+{
+    if (a == 0) return side ? p->bcx_hi : p->bcx_lo;
+    if (a == 1) return side ? p->bc_hi : p->bc_lo;
+    return side ? p->bcz_hi : p->bcz_lo;
+}
+
+/* Whether node (x, y, z) lies on a face that is not periodic. */
+static int on_wall(const orc_params* p, int64_t x, int64_t y, int64_t z)
+{
+    return (p->bcx_lo != ORC_PERIODIC && (x == 0 || x == p->nx - 1)) ||
+           (p->bc_lo != ORC_PERIODIC && (y == 0 || y == p->ny - 1)) ||
+           (p->bcz_lo != ORC_PERIODIC && (z == 0 || z == p->nz - 1));
+}
+
+static int any_wall(const orc_params* p)
+{
+    return p->bc_lo != ORC_PERIODIC || p->bcx_lo != ORC_PERIODIC || p->bcz_lo != ORC_PERIODIC;
+}
+
+/* The population whose velocity is e_i reflected in the axes whose bit is set in mask. */
+static int reflect(const orc_lattice* L, int i, int mask)
+{
+    int e[3];
+    for (int a = 0; a < 3; ++a) e[a] = (mask >> a & 1) ? -L->e[i][a] : L->e[i][a];
+    for (int j = 0; j < L->q; ++j)
+        if (L->e[j][0] == e[0] && L->e[j][1] == e[1] && L->e[j][2] == e[2]) return j;
+    return -1;
+}
+
+/* For population i at node (x, y, z): the faces its pull source x - e_i lies
+ * beyond (bit a set for axis a), with the kinds found there: *bb = 1 if one of
+ * them is BOUNCEBACK, *nf = mask of the NOFLUX_NODE ones. */
+static int beyond(const orc_lattice* L, const orc_params* p, int i, int64_t x, int64_t y, int64_t z, int* bb,
+                  int* nf)
+{
+    const int64_t c[3] = {x, y, z}, n[3] = {p->nx, p->ny, p->nz};
+    int mask = 0;
+    *bb = 0;
+    *nf = 0;
+    for (int a = 0; a < 3; ++a) {
+        const int e = L->e[i][a];
+        if (e == 0) continue;
+        const int side = e > 0 ? 0 : 1;   /* e > 0: the source lies below the low face */
+        const int kind = face_kind(p, a, side);
+        if (kind == ORC_PERIODIC) continue;
+        if ((e > 0 && c[a] == 0) || (e < 0 && c[a] == n[a] - 1)) {
+            mask |= 1 << a;
+            if (kind == ORC_BOUNCEBACK) *bb = 1;
+            if (kind == ORC_NOFLUX_NODE) *nf |= 1 << a;
+        }
+    }
+    return mask;
+}
+
 static void set_threads(const orc_params* p)
 {
 #ifdef _OPENMP
@@ -432,42 +501,54 @@ int orc_phi(const orc_params* p, const double* f, double* phi)
     return 0;
 }
 
-/* Wall rules at the wall nodes y = 0 and y = ny-1, after streaming.
+/* Wall rules at the wall nodes, after streaming (and after the bounce-back of
+ * the push):
  *   NOFLUX_NODE: the Neumann rule of Sec. 3.2 (bottom f2=f4, f5=f8, f6=f7;
- *                top f4=f2, f7=f6, f8=f5), i.e. every population whose source
- *                lies beyond the wall copies its mirror image in y.
- *   DIRICHLET:   every population whose source lies beyond the wall is set to
- *                f^eq_i(phi*, u) with phi* chosen so that sum_i f_i = phi_w.
+ *                top f4=f2, f7=f6, f8=f5): a population whose source lies beyond
+ *                Neumann walls copies the population reflected in the axes of
+ *                those walls (on the y faces alone: its mirror image in y; at an
+ *                edge of two Neumann faces, the population reflected in both).
+ *   DIRICHLET:   (y faces only) every population whose source lies beyond the
+ *                wall is set to f^eq_i(phi*, u) with phi* chosen so that
+ *                sum_i f_i = phi_w.
  *   BOUNCEBACK is applied during the push itself. */
 static void wall_fill(const orc_lattice* L, const orc_params* p, const double* u, double* fn)
 {
     const int64_t nx = p->nx, ny = p->ny, nz = p->nz, nc = ncells(p);
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                if (!on_wall(p, x, y, z)) continue;
+                const int64_t c = x + nx * (y + ny * z);
+                double v[ORC_MAXQ];
+                for (int i = 0; i < L->q; ++i) v[i] = fn[i * nc + c];
+                for (int i = 0; i < L->q; ++i) {
+                    int bb, nf;
+                    beyond(L, p, i, x, y, z, &bb, &nf);
+                    if (nf) fn[i * nc + c] = v[reflect(L, i, nf)];
+                }
+            }
     for (int side = 0; side < 2; ++side) {
         const int kind = side == 0 ? p->bc_lo : p->bc_hi;
-        if (kind != ORC_NOFLUX_NODE && kind != ORC_DIRICHLET) continue;
+        if (kind != ORC_DIRICHLET) continue;
         const int64_t y = side == 0 ? 0 : ny - 1;
         const int inward = side == 0 ? +1 : -1; /* e_y of the unknown populations */
         for (int64_t z = 0; z < nz; ++z)
             for (int64_t x = 0; x < nx; ++x) {
                 const int64_t c = x + nx * (y + ny * z);
-                if (kind == ORC_NOFLUX_NODE) {
-                    for (int i = 0; i < L->q; ++i)
-                        if (L->e[i][1] == inward) fn[i * nc + c] = fn[mirror_y(L, i) * nc + c];
-                } else {
-                    double uu[3], me[ORC_MAXQ], w[ORC_MAXQ];
-                    get_u(L, u, nc, c, uu);
-                    meq(L, p, 1.0, uu, me);
-                    matvec(L->q, L->Minv, me, w); /* f^eq at unit phi */
-                    double known = 0.0, wk = 0.0;
-                    for (int i = 0; i < L->q; ++i) {
-                        if (L->e[i][1] == inward) wk += w[i];
-                        else known += fn[i * nc + c];
-                    }
-                    const double phiw = side == 0 ? p->phi_w_lo : p->phi_w_hi;
-                    const double phis = (phiw - known) / wk;
-                    for (int i = 0; i < L->q; ++i)
-                        if (L->e[i][1] == inward) fn[i * nc + c] = phis * w[i];
+                double uu[3], me[ORC_MAXQ], w[ORC_MAXQ];
+                get_u(L, u, nc, c, uu);
+                meq(L, p, 1.0, uu, me);
+                matvec(L->q, L->Minv, me, w); /* f^eq at unit phi */
+                double known = 0.0, wk = 0.0;
+                for (int i = 0; i < L->q; ++i) {
+                    if (L->e[i][1] == inward) wk += w[i];
+                    else known += fn[i * nc + c];
                 }
+                const double phiw = side == 0 ? p->phi_w_lo : p->phi_w_hi;
+                const double phis = (phiw - known) / wk;
+                for (int i = 0; i < L->q; ++i)
+                    if (L->e[i][1] == inward) fn[i * nc + c] = phis * w[i];
             }
     }
 }
@@ -493,41 +574,47 @@ int orc_step(const orc_params* p, const double* f_in, const double* u, double* f
         for (int i = 0; i < q; ++i) fpost[i * nc + c] = fo[i];
     }
     for (int64_t k = 0; k < (int64_t)q * nc; ++k) f_out[k] = 0.0;
-    const int periodic_y = (p->bc_lo == ORC_PERIODIC);
+    const int per[3] = {p->bcx_lo == ORC_PERIODIC, p->bc_lo == ORC_PERIODIC, p->bcz_lo == ORC_PERIODIC};
+    const int64_t n[3] = {nx, ny, nz};
     int opp[ORC_MAXQ];
     for (int i = 0; i < q; ++i) opp[i] = opposite(&L, i);
     /* Eq. 5: f_i(x + e_i, t + 1) = f'_i(x, t).  Parallel over destination
-     * planes i: each plane is written by exactly one thread, except that
-     * bounce-back writes plane opp(i); that case runs serially below. */
+     * planes i: each plane is written by exactly one thread; populations that
+     * would leave through a wall are left to the serial pass below. */
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < q; ++i) {
         for (int64_t z = 0; z < nz; ++z)
             for (int64_t y = 0; y < ny; ++y)
                 for (int64_t x = 0; x < nx; ++x) {
                     const int64_t c = x + nx * (y + ny * z);
-                    int64_t yd = y + L.e[i][1];
-                    if (periodic_y) yd = wrap(yd, ny);
-                    else if (yd < 0 || yd >= ny) continue; /* leaves through a wall */
-                    const int64_t xd = wrap(x + L.e[i][0], nx);
-                    const int64_t zd = wrap(z + L.e[i][2], nz);
-                    f_out[i * nc + xd + nx * (yd + ny * zd)] = fpost[i * nc + c];
+                    const int64_t r[3] = {x, y, z};
+                    int64_t d[3];
+                    int out = 0;
+                    for (int a = 0; a < 3; ++a) {
+                        d[a] = r[a] + L.e[i][a];
+                        if (per[a]) d[a] = wrap(d[a], n[a]);
+                        else if (d[a] < 0 || d[a] >= n[a]) out = 1; /* leaves through a wall */
+                    }
+                    if (out) continue;
+                    f_out[i * nc + d[0] + nx * (d[1] + ny * d[2])] = fpost[i * nc + c];
                 }
     }
-    if (!periodic_y) {
-        /* Halfway bounce-back: a population leaving through a BOUNCEBACK wall
-         * returns to its node in the opposite direction. */
-        for (int side = 0; side < 2; ++side) {
-            const int kind = side == 0 ? p->bc_lo : p->bc_hi;
-            if (kind != ORC_BOUNCEBACK) continue;
-            const int64_t y = side == 0 ? 0 : ny - 1;
-            const int outward = side == 0 ? -1 : +1;
-            for (int64_t z = 0; z < nz; ++z)
+    if (any_wall(p)) {
+        /* Halfway bounce-back: a population that would leave through a wall of
+         * which (one) is BOUNCEBACK returns to its node in the opposite
+         * direction; the population opp(i) there has its source beyond the same
+         * faces, so nothing else writes it. */
+        for (int64_t z = 0; z < nz; ++z)
+            for (int64_t y = 0; y < ny; ++y)
                 for (int64_t x = 0; x < nx; ++x) {
+                    if (!on_wall(p, x, y, z)) continue;
                     const int64_t c = x + nx * (y + ny * z);
-                    for (int i = 0; i < q; ++i)
-                        if (L.e[i][1] == outward) f_out[opp[i] * nc + c] = fpost[i * nc + c];
+                    for (int i = 0; i < q; ++i) {
+                        int bb, nf;
+                        if (beyond(&L, p, opp[i], x, y, z, &bb, &nf) && bb)
+                            f_out[opp[i] * nc + c] = fpost[i * nc + c];
+                    }
                 }
-        }
         wall_fill(&L, p, u, f_out);
     }
     return 0;
@@ -600,6 +687,7 @@ int orc_adjoint_step(const orc_params* p, const double* lam_next, const double* 
     int rc = build_lattice(&L, p);
     if (rc) return rc;
     if (p->bc_lo == ORC_DIRICHLET || p->bc_hi == ORC_DIRICHLET) return -4;
+    if (p->bcx_lo != ORC_PERIODIC || p->bcz_lo != ORC_PERIODIC) return -4;  /* y-face walls only */
     const int64_t nx = p->nx, ny = p->ny, nz = p->nz, nc = ncells(p);
     const int q = L.q;
     const int periodic_y = (p->bc_lo == ORC_PERIODIC);

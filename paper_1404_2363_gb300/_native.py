@@ -45,6 +45,10 @@ class LbmDesc(ctypes.Structure):
         ("alloc_ctx", ctypes.c_void_p),
         ("stream", ctypes.c_void_p),
         ("model", ctypes.c_int32),
+        ("bc_lo_x", ctypes.c_int32),
+        ("bc_hi_x", ctypes.c_int32),
+        ("bc_lo_z", ctypes.c_int32),
+        ("bc_hi_z", ctypes.c_int32),
     ]
 
 

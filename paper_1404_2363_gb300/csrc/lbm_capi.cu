@@ -56,6 +56,7 @@ struct lbm_cde_s {
     // TMA-staged D2Q9 step (launch vec 7): tensor maps per source buffer, and the
     // device status word its bounded waits report to
     lbm::TmaMaps tmaps[2];
+    lbm::TmaMaps15 tmaps15[2];
     bool tmaps_ok = false;
     const float* tmaps_ua = nullptr;
     int* status_dev = nullptr;
@@ -231,21 +232,29 @@ static StepArgs make_args(lbm_cde_t h, int src_idx)
     a.bc_hi = h->d.bc_hi_y;
     a.phiw_lo = (float)h->d.phi_w_lo_y;
     a.phiw_hi = (float)h->d.phi_w_hi_y;
+    a.bcx_lo = h->d.bc_lo_x;
+    a.bcx_hi = h->d.bc_hi_x;
+    a.bcz_lo = h->d.bc_lo_z;
+    a.bcz_hi = h->d.bc_hi_z;
     a.c = h->coef;
     a.status = h->status_dev;
     a.spin_limit = h->wait_limit;
     return a;
 }
 
-// Tensor maps for the TMA-staged step, re-encoded when the velocity field changes.
+// Tensor maps for the TMA-staged steps, re-encoded when the velocity field changes.
 static lbm_status ensure_tma_maps(lbm_cde_t h)
 {
     const float* ua = h->ukind == LBM_U_FIELD ? h->ua : nullptr;
     if (h->tmaps_ok && h->tmaps_ua == ua) return LBM_OK;
     h->tmaps_ok = false;
-    for (int b = 0; b < 2; ++b)
-        if (!lbm::encode_tma_maps(h->state[b], h->phi[b], ua, (int)h->d.nx, (int)h->d.ny, &h->tmaps[b]))
-            return fail(h, LBM_E_CUDA, "tensor map encoding failed (launch vec 7 / 8)");
+    for (int b = 0; b < 2; ++b) {
+        const bool ok = h->q == 9 ? lbm::encode_tma_maps(h->state[b], h->phi[b], ua, (int)h->d.nx, (int)h->d.ny,
+                                                         &h->tmaps[b])
+                                  : lbm::encode_tma_maps15(h->state[b], h->phi[b], ua, (int)h->d.nx, (int)h->d.ny,
+                                                           (int)h->d.nz, &h->tmaps15[b]);
+        if (!ok) return fail(h, LBM_E_CUDA, "tensor map encoding failed (launch vec 7 / 8)");
+    }
     h->tmaps_ok = true;
     h->tmaps_ua = ua;
     return LBM_OK;
@@ -285,6 +294,7 @@ lbm_status lbm_cde_desc_init(lbm_cde_desc* d, int32_t lattice, int64_t nx, int64
     d->ny = ny;
     d->nz = nz;
     d->bc_lo_y = d->bc_hi_y = LBM_BC_PERIODIC;
+    d->bc_lo_x = d->bc_hi_x = d->bc_lo_z = d->bc_hi_z = LBM_BC_PERIODIC;
     d->alpha1 = d->alpha2 = NAN;
     for (int k = 0; k < 15; ++k) d->s[k] = NAN;
     d->tie_q_rates = 1;
@@ -314,6 +324,19 @@ lbm_status lbm_cde_create(const lbm_cde_desc* desc, lbm_cde_t* out)
         return fail(nullptr, LBM_E_ARG, "periodic y needs both y faces periodic");
     if (d.bc_lo_y != LBM_BC_PERIODIC && d.ny < 3)
         return fail(nullptr, LBM_E_ARG, "walls need ny >= 3");
+    {
+        const int fx[2] = {d.bc_lo_x, d.bc_hi_x}, fz[2] = {d.bc_lo_z, d.bc_hi_z};
+        for (int k = 0; k < 2; ++k)
+            if (fx[k] < LBM_BC_PERIODIC || fx[k] > LBM_BC_BOUNCEBACK || fz[k] < LBM_BC_PERIODIC ||
+                fz[k] > LBM_BC_BOUNCEBACK)
+                return fail(nullptr, LBM_E_ARG, "x and z faces take PERIODIC, NOFLUX_NODE or BOUNCEBACK");
+        if ((fx[0] == LBM_BC_PERIODIC) != (fx[1] == LBM_BC_PERIODIC) ||
+            (fz[0] == LBM_BC_PERIODIC) != (fz[1] == LBM_BC_PERIODIC))
+            return fail(nullptr, LBM_E_ARG, "periodic x (z) needs both x (z) faces periodic");
+        if (fx[0] != LBM_BC_PERIODIC && d.nx < 3) return fail(nullptr, LBM_E_ARG, "x walls need nx >= 3");
+        if (fz[0] != LBM_BC_PERIODIC && (d.lattice != LBM_D3Q15 || d.nz < 3))
+            return fail(nullptr, LBM_E_ARG, "z walls need D3Q15 and nz >= 3");
+    }
     if ((d.alloc == nullptr) != (d.free_ == nullptr))
         return fail(nullptr, LBM_E_ARG, "alloc and free_ must both be set or both NULL");
     if (d.model < LBM_MRT_A || d.model > LBM_MRT_B3) return fail(nullptr, LBM_E_ARG, "bad model");
@@ -487,14 +510,15 @@ lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps)
     if (!h->ready) return fail(h, LBM_E_STATE, "set_phi must come before step");
     const bool walls = h->d.bc_lo_y != LBM_BC_PERIODIC;
     const int uk = ukind_internal(h->ukind);
-    const bool tma = (h->cfg.vec == 7 || h->cfg.vec == 8) && h->q == 9 && h->neq;
+    const bool tma = (h->cfg.vec == 7 || h->cfg.vec == 8) && h->neq;
     if (tma) {
         const lbm_status ts = ensure_tma_maps(h);
         if (ts != LBM_OK) return ts;
     }
     for (int64_t n = 0; n < nsteps; ++n) {
         StepArgs a = make_args(h, h->cur);
-        if (tma) a.tma = &h->tmaps[h->cur];
+        if (tma && h->q == 9) a.tma = &h->tmaps[h->cur];
+        if (tma && h->q == 15) a.tma15 = &h->tmaps15[h->cur];
         CK(h, lbm::launch_step(h->q, h->d.storage, uk, walls, h->cfg, a, h->st));
         h->cur ^= 1;
         h->t += 1;
@@ -515,10 +539,12 @@ lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec)
     const bool tile_ok = h->d.nx % 32 == 0 && h->d.ny % 8 == 0;
     const bool pair_ok = h->neq && h->d.nx % 2 == 0 && (long long)(h->q + 3) * h->ncell < (1LL << 31);
     const bool quad = h->q == 9 && h->d.nx % 4 == 0 && 12LL * h->ncell < (1LL << 31);
-    const bool tma = h->q == 9 && h->neq && h->d.nx % 256 == 0 && 12LL * h->ncell < (1LL << 31);
+    const bool tma = h->neq && ((h->q == 9 && h->d.nx % 256 == 0 && 12LL * h->ncell < (1LL << 31)) ||
+                                (h->q == 15 && h->d.nx % 128 == 0 && 18LL * h->ncell < (1LL << 31)));
     if (vec == 7 || vec == 8) {
         if (block != 128 || !tma)
-            return fail(h, LBM_E_ARG, "vec 7 / 8 (TMA-staged D2Q9 16-bit kernel) needs block 128 and nx % 256 == 0");
+            return fail(h, LBM_E_ARG, "vec 7 / 8 (TMA-staged 16-bit kernels) needs block 128 and nx % 256 == 0 "
+                                      "(D2Q9) or nx % 128 == 0 (D3Q15)");
         h->cfg.block = block;
         h->cfg.vec = vec;
         return LBM_OK;
@@ -551,8 +577,9 @@ static std::string tune_key(lbm_cde_t h)
     for (char& ch : gpu)
         if (ch == ' ') ch = '_';
     char buf[256];
-    snprintf(buf, sizeof(buf), "q%d_s%d_%lldx%lldx%lld_u%d_bc%d%d_%s", h->q, h->d.storage, (long long)h->d.nx,
-             (long long)h->d.ny, (long long)h->d.nz, h->ukind, h->d.bc_lo_y, h->d.bc_hi_y, gpu.c_str());
+    snprintf(buf, sizeof(buf), "q%d_s%d_%lldx%lldx%lld_u%d_bc%d%d%d%d%d%d_%s", h->q, h->d.storage,
+             (long long)h->d.nx, (long long)h->d.ny, (long long)h->d.nz, h->ukind, h->d.bc_lo_y, h->d.bc_hi_y,
+             h->d.bc_lo_x, h->d.bc_hi_x, h->d.bc_lo_z, h->d.bc_hi_z, gpu.c_str());
     return buf;
 }
 
@@ -629,7 +656,8 @@ lbm_status lbm_cde_autotune(lbm_cde_t h, int64_t steps, int32_t* block_out, int3
         for (int b : {64, 96, 128, 192, 256}) cand.push_back(LaunchCfg{b, 5});
     if (h->q == 9 && h->d.nx % 4 == 0 && 12LL * h->ncell < (1LL << 31))
         for (int b : {64, 128, 256}) cand.push_back(LaunchCfg{b, 6});
-    if (h->q == 9 && h->neq && h->d.nx % 256 == 0 && 12LL * h->ncell < (1LL << 31) &&
+    if (h->neq && ((h->q == 9 && h->d.nx % 256 == 0 && 12LL * h->ncell < (1LL << 31)) ||
+                   (h->q == 15 && h->d.nx % 128 == 0 && 18LL * h->ncell < (1LL << 31))) &&
         ensure_tma_maps(h) == LBM_OK) {   // tensor maps available
         cand.push_back(LaunchCfg{128, 7});
         cand.push_back(LaunchCfg{128, 8});
@@ -765,6 +793,8 @@ static lbm_status adjoint_supported(lbm_cde_t h)
         return fail(h, LBM_E_UNSUPPORTED, "the adjoint needs FP32 state storage");
     if (h->d.bc_lo_y == LBM_BC_DIRICHLET || h->d.bc_hi_y == LBM_BC_DIRICHLET)
         return fail(h, LBM_E_UNSUPPORTED, "the adjoint does not support Dirichlet walls");
+    if (h->d.bc_lo_x != LBM_BC_PERIODIC || h->d.bc_lo_z != LBM_BC_PERIODIC)
+        return fail(h, LBM_E_UNSUPPORTED, "the adjoint supports walls on the y faces only");
     if (!h->d_set) return fail(h, LBM_E_STATE, "set_D must come first");
     return LBM_OK;
 }

@@ -561,6 +561,124 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// The step with walls on the x (and z) faces as well (any storage, one node per
+// thread; the other kernels take periodic x and z). For each population i the
+// pull source x - e_i is checked against every face; a source beyond a face
+// whose axis is not periodic is not read:
+//   - if one of the faces it lies beyond is BOUNCEBACK, f_i = f'_opp(i) of the
+//     node itself (halfway bounce-back);
+//   - then, if it lies beyond NOFLUX_NODE faces, f_i takes the value of the
+//     population reflected in the axes of those faces (the Sec. 3.2 mirror rule,
+//     applied per axis; at an edge of two Neumann faces, reflected in both);
+//   - Dirichlet (y faces only) replaces every population entering from beyond
+//     the y wall, as in k_step.
+// ---------------------------------------------------------------------------
+template <class L>
+__device__ __forceinline__ int reflect_mask(int i, int mask)
+{
+    const int e[3] = {(mask & 1) ? -L::ex(i) : L::ex(i), (mask & 2) ? -L::ey(i) : L::ey(i),
+                      (mask & 4) ? -L::ez(i) : L::ez(i)};
+    int r = i;
+#pragma unroll
+    for (int j = 0; j < L::Q; ++j)
+        if (L::ex(j) == e[0] && L::ey(j) == e[1] && L::ez(j) == e[2]) r = j;
+    return r;
+}
+
+template <class L, int STORE, int UK, typename IX>
+__global__ void __launch_bounds__(256) k_step_box(const StepArgs a)
+{
+    using T = typename StT<STORE>::T;
+    constexpr int Q = L::Q;
+    constexpr bool NEQ = (STORE != ST_F32);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= nx) return;
+    const IX N = (IX)a.ncell;
+    const T* __restrict__ src = static_cast<const T*>(a.src);
+    T* __restrict__ dst = static_cast<T*>(a.dst);
+    const int pos[3] = {x, y, z}, n[3] = {nx, ny, nz};
+    const int klo[3] = {a.bcx_lo, a.bc_lo, a.bcz_lo}, khi[3] = {a.bcx_hi, a.bc_hi, a.bcz_hi};
+    const IX cell = (IX)x + (IX)nx * ((IX)y + (IX)ny * (IX)z);
+    float s_now[3], s_prev[3];
+    if (UK != U_NONE) {
+        sched_row_at(a.sched, a.srow_now, L::DIM, s_now);
+        sched_row_at(a.sched, a.srow_prev, L::DIM, s_prev);
+    }
+    float uxp = 0.f, uyp = 0.f, uzp = 0.f;   // u(k - 1) at the node (bounce-back decode, Dirichlet)
+    vel_ix<UK, L::DIM, IX>(a, N, cell, y, s_prev, uxp, uyp, uzp);
+    float w[Q];
+    int nf[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int e[3] = {L::ex(i), L::ey(i), L::ez(i)};
+        int sp[3];
+        bool out = false, bb = false;
+        nf[i] = 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            sp[d] = pos[d] - e[d];
+            if (e[d] == 0) continue;
+            if (klo[d] == BC_PERIODIC) {
+                sp[d] = sp[d] < 0 ? sp[d] + n[d] : (sp[d] >= n[d] ? sp[d] - n[d] : sp[d]);
+            } else if (sp[d] < 0 || sp[d] >= n[d]) {
+                const int kind = sp[d] < 0 ? klo[d] : khi[d];
+                out = true;
+                bb = bb || kind == BC_BOUNCE;
+                if (kind == BC_NOFLUX) nf[i] |= 1 << d;
+            }
+        }
+        float v = 0.f;
+        if (!out) {
+            const IX sc = (IX)sp[0] + (IX)nx * ((IX)sp[1] + (IX)ny * (IX)sp[2]);
+            v = ldg_f(src + (IX)i * N + sc);
+            if (NEQ) {
+                float ux, uy, uz;
+                vel_ix<UK, L::DIM, IX>(a, N, sc, sp[1], s_prev, ux, uy, uz);
+                v = fmaf(__ldg(a.phi_src + sc), feq_unit<L>(a.c, i, ux, uy, uz), v);
+            }
+        } else if (bb) {
+            const int o = opposite<L>(i);
+            v = ldg_f(src + (IX)o * N + cell);
+            if (NEQ) v = fmaf(__ldg(a.phi_src + cell), feq_unit<L>(a.c, o, uxp, uyp, uzp), v);
+        }
+        w[i] = v;
+    }
+    float f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        f[i] = w[i];
+        if (nf[i]) {
+            const int j = reflect_mask<L>(i, nf[i]);
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+                if (k == j) f[i] = w[k];
+        }
+    }
+    const bool lo = y == 0 && a.bc_lo == BC_DIRICHLET, hi = y == ny - 1 && a.bc_hi == BC_DIRICHLET;
+    if (lo || hi) {
+        const int inward = lo ? 1 : -1;
+        float known = 0.f, wk = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (L::ey(i) == inward) wk += feq_unit<L>(a.c, i, uxp, uyp, uzp);
+            else known += f[i];
+        }
+        const float ps = ((lo ? a.phiw_lo : a.phiw_hi) - known) / wk;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if (L::ey(i) == inward) f[i] = __fmul_rn(ps, feq_unit<L>(a.c, i, uxp, uyp, uzp));
+    }
+    float ux, uy, uz;
+    vel_ix<UK, L::DIM, IX>(a, N, cell, y, s_now, ux, uy, uz);
+    const float phi = collide<L, NEQ>(f, ux, uy, uz, a.c);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st_f(dst + (IX)i * N + cell, f[i]);
+    if (NEQ) a.phi_dst[cell] = phi;
+}
+
+// ---------------------------------------------------------------------------
 // D2Q9 step for the 16-bit offset storage. The decode
 //     f_i = g_i(s_i) + w_i phi(s_i) + k_i e_i . (phi u)(s_i),   s_i = x - e_i,
 // needs phi and phi u(k-1) at all nine pull sources. A thread owns one column

@@ -65,6 +65,19 @@ struct TmaMaps {
     CUtensorMap u, uh;    // velocity factors [2][ny][nx]: boxes (256, 1, 2) and (4, 1, 2)
 };
 
+// Tensor maps of the TMA-staged D3Q15 step (k_step_tma_d3q15) for one source
+// buffer; 16-bit offsets as the 4-D tensor [15][nz][ny][nx], phi [nz][ny][nx],
+// velocity factors [3][nz][ny][nx].
+struct TmaMaps15 {
+    CUtensorMap gA;   // offsets, box (128, 1, 1, 5): planes 0 .. 4 (e_z = 0)
+    CUtensorMap gB;   // offsets, box (128, 1, 1, 1): plane 5 or 6 (z axis)
+    CUtensorMap gC;   // offsets, box (128, 1, 1, 4): corners 7 .. 10 or 11 .. 14
+    CUtensorMap hA;   // offsets, box (8, 1, 1, 2): halo of planes 1, 2 (x axis)
+    CUtensorMap hC;   // offsets, box (8, 1, 1, 4): halo of four corners
+    CUtensorMap p, ph;   // phi: boxes (128, 1, 1) and (4, 1, 1)
+    CUtensorMap u, uh;   // velocity factors: boxes (128, 1, 1, 3) and (4, 1, 1, 3)
+};
+
 struct StepArgs {
     const void* src;      // state planes [q][ncell] (float or 16-bit)
     void* dst;
@@ -78,12 +91,15 @@ struct StepArgs {
     int srow_prev;        // (k-1) mod sched_len, or -1 without a schedule
     int nx, ny, nz;
     long long ncell;
-    int bc_lo, bc_hi;
+    int bc_lo, bc_hi;     // y faces
     float phiw_lo, phiw_hi;
+    int bcx_lo, bcx_hi;   // x faces (k_step_box only)
+    int bcz_lo, bcz_hi;   // z faces (k_step_box only)
     Coef c;
     int* status;          // device status word (LBM_E_TIMEOUT from a bounded wait) or nullptr
     long long spin_limit; // SM clock cycles a bounded wait may take (0: give up at once)
     const TmaMaps* tma;   // host pointer: tensor maps of src / phi_src / ua, or nullptr
+    const TmaMaps15* tma15;   // the same for the D3Q15 kernel, or nullptr
 };
 
 // One reverse-time step (lbm_adjoint.cu).
@@ -147,9 +163,18 @@ inline bool tma_ok(const StepArgs& a, int ukind)
            (ukind != U_FIELD || (reinterpret_cast<uintptr_t>(a.ua) & 15) == 0);
 }
 
-// Encodes the tensor maps for one source buffer (lbm_tma.cu); false if the
+// The TMA-staged D3Q15 kernel needs 128-column strips (nx % 128 == 0), int
+// offsets, a 16-byte aligned velocity field and the tensor maps of the source.
+inline bool tma15_ok(const StepArgs& a, int ukind)
+{
+    return a.tma15 != nullptr && a.nx % 128 == 0 && 18LL * a.ncell < (1LL << 31) &&
+           (ukind != U_FIELD || (reinterpret_cast<uintptr_t>(a.ua) & 15) == 0);
+}
+
+// Encode the tensor maps for one source buffer (lbm_tma.cu); false if the
 // driver entry point is missing or the layout breaks a tensor-map rule.
 bool encode_tma_maps(const void* g, const float* phi, const float* ua, int nx, int ny, TmaMaps* out);
+bool encode_tma_maps15(const void* g, const float* phi, const float* ua, int nx, int ny, int nz, TmaMaps15* out);
 
 struct LaunchCfg {
     int block;   // threads per block (multiple of 32)

@@ -5,12 +5,20 @@
 #include "lbm_pair.cuh"
 #include "lbm_pair_d3q15.cuh"
 #include "lbm_tma_d2q9.cuh"
+#include "lbm_tma_d3q15.cuh"
 
 namespace lbm {
 
 template <class L, int STORE, int UK, bool WALLS>
 static cudaError_t step_vec(LaunchCfg cfg, const StepArgs& a, cudaStream_t st)
 {
+    if (a.bcx_lo != BC_PERIODIC || a.bcz_lo != BC_PERIODIC) {
+        // walls on the x or z faces: the general one-node kernel, whatever the launch shape
+        dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)a.ny, (unsigned)a.nz);
+        if ((long long)(L::Q + 3) * a.ncell < (1LL << 31)) k_step_box<L, STORE, UK, int><<<grid, 256, 0, st>>>(a);
+        else k_step_box<L, STORE, UK, long long><<<grid, 256, 0, st>>>(a);
+        return cudaGetLastError();
+    }
     if constexpr (L::Q == 9) {
         if (cfg.vec == 6 && quad_ok(a, UK)) {
             // node-quad variant: 128-bit / 64-bit vector loads and stores, four nodes per thread
@@ -21,6 +29,9 @@ static cudaError_t step_vec(LaunchCfg cfg, const StepArgs& a, cudaStream_t st)
         }
     }
     if constexpr (L::Q == 15 && STORE != ST_F32) {
+        // TMA-staged rows: two rows per iteration and five stages, or four and seven
+        if (cfg.vec == 7 && tma15_ok(a, UK)) return launch_tma_d3q15<STORE, UK, WALLS, 2, 5>(a, st);
+        if (cfg.vec == 8 && tma15_ok(a, UK)) return launch_tma_d3q15<STORE, UK, WALLS, 4, 7>(a, st);
         if (cfg.vec == 5 && pair_ok(a, UK, L::Q)) {
             // node-pair variant (paired FP32 arithmetic, two adjacent nodes per thread)
             const int per = 2 * cfg.block;

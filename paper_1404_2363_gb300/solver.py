@@ -43,14 +43,16 @@ class Solver:
     """One lattice Boltzmann solver instance on one GPU.
 
     Parameters mirror ``lbm_cde_desc``: lattice 9 (D2Q9) or 15 (D3Q15), grid
-    (nx, ny, nz), storage 'f32' | 'f16' | 'bf16', wall kinds for the y faces,
+    (nx, ny, nz), storage 'f32' | 'f16' | 'bf16', wall kinds for the y faces
+    (``bc``) and for the x and z faces (``bc_x``, ``bc_z``: periodic, noflux or
+    bounceback),
     Dirichlet values, optional alpha1/alpha2 and diagonal rates ``s`` (None
     entries keep the defaults).
     """
 
     def __init__(self, lattice=9, nx=64, ny=64, nz=1, storage="f32", bc=("periodic", "periodic"),
                  phi_w=(0.0, 0.0), alpha=None, s=None, tie=True, device=None, stream=None,
-                 torch_alloc=True, model="A"):
+                 torch_alloc=True, model="A", bc_x=("periodic", "periodic"), bc_z=("periodic", "periodic")):
         self.L = N.lib()
         if device is None:
             device = torch.device("cuda", torch.cuda.current_device())
@@ -66,6 +68,8 @@ class Solver:
         N.check(self.L.lbm_cde_desc_init(ctypes.byref(d), lattice, nx, ny, nz), "desc_init")
         d.storage = STORAGE[storage]
         d.bc_lo_y, d.bc_hi_y = BC[bc[0]], BC[bc[1]]
+        d.bc_lo_x, d.bc_hi_x = BC[bc_x[0]], BC[bc_x[1]]
+        d.bc_lo_z, d.bc_hi_z = BC[bc_z[0]], BC[bc_z[1]]
         d.phi_w_lo_y, d.phi_w_hi_y = float(phi_w[0]), float(phi_w[1])
         if alpha is not None:
             d.alpha1, d.alpha2 = float(alpha[0]), float(alpha[1])

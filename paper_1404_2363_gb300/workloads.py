@@ -159,12 +159,14 @@ def random_rotation(g: np.random.Generator) -> np.ndarray:
     return Q
 
 
-def curl_field_3d(n: int, g: np.random.Generator, kmax: int = 4, umax: float = 0.05) -> np.ndarray:
+def curl_field_3d(n: int, g: np.random.Generator, kmax: int = 4, umax: float = 0.05, shape=None) -> np.ndarray:
     """Divergence-free u = curl(psi), psi a random Fourier vector potential with
-    integer wave-vectors |k|_inf <= kmax; shape (3, n, n, n) in [z, y, x] order."""
-    j = np.arange(n) * (2.0 * math.pi / n)
-    Z, Y, X = np.meshgrid(j, j, j, indexing="ij")
-    u = np.zeros((3, n, n, n))
+    integer wave-vectors |k|_inf <= kmax (per period of each axis); shape
+    (3, nz, ny, nx) in [z, y, x] order, nx = ny = nz = n unless shape = (nx, ny, nz)."""
+    nx, ny, nz = (n, n, n) if shape is None else shape
+    jx, jy, jz = (np.arange(m) * (2.0 * math.pi / m) for m in (nx, ny, nz))
+    Z, Y, X = np.meshgrid(jz, jy, jx, indexing="ij")
+    u = np.zeros((3, nz, ny, nx))
     nmodes = 12
     for _ in range(nmodes):
         k = g.integers(-kmax, kmax + 1, size=3)
@@ -175,22 +177,26 @@ def curl_field_3d(n: int, g: np.random.Generator, kmax: int = 4, umax: float = 0
         arg = k[0] * X + k[1] * Y + k[2] * Z + ph
         c = np.cos(arg)
         # curl of amp * sin(arg) = (k x amp) cos(arg)
-        kx = np.cross(k.astype(np.float64), amp)
+        # the curl in grid units: d/dx of arg is 2 pi k_x / nx (= k_x 2 pi / n on a cube)
+        kg = k.astype(np.float64) * (2.0 * math.pi) / np.array([nx, ny, nz], dtype=np.float64)
+        kx = np.cross(kg, amp)
         for a in range(3):
             u[a] += kx[a] * c
     m = np.sqrt((u * u).sum(axis=0)).max()
     return u * (umax / m)
 
 
-def d3q15_workload(n: int = 384):
+def d3q15_workload(n: int = 384, shape=None):
+    """The D3Q15 hill on an n^3 grid, or on nx x ny x nz for shape = (nx, ny, nz)
+    (sigma0 = 0.025 of the shortest side)."""
+    nx, ny, nz = (n, n, n) if shape is None else shape
     g = rng(4)
     lam = g.uniform(0.01, 0.05, size=3)
     Q = random_rotation(g)
     D = Q @ np.diag(lam) @ Q.T
-    u = curl_field_3d(n, g)
-    s = 0.025 * n
-    j = np.arange(n) - n // 2
-    Z, Y, X = np.meshgrid(j, j, j, indexing="ij")
+    u = curl_field_3d(n, g, shape=shape)
+    s = 0.025 * min(nx, ny, nz)
+    Z, Y, X = np.meshgrid(np.arange(nz) - nz // 2, np.arange(ny) - ny // 2, np.arange(nx) - nx // 2, indexing="ij")
     phi0 = np.exp(-(X * X + Y * Y + Z * Z) / (2 * s * s))
     return {"phi0": phi0, "D": D, "u": u}
 

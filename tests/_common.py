@@ -28,6 +28,9 @@ class Case:
     umax: float = 0.05
     seed: int = 0
     model: str = "A"
+    bg: bool = True               # False: the hill alone, no positive background
+    bc_x: tuple = ("periodic", "periodic")
+    bc_z: tuple = ("periodic", "periodic")
 
     @property
     def dim(self):
@@ -40,15 +43,26 @@ class Case:
     def inputs(self):
         g = np.random.default_rng(1234 + self.seed)
         if self.lattice == 9:
-            phi0 = W.gaussian_phi0(self.nx, self.ny, max(self.nx, self.ny) / 8.0) + 0.2 + 0.1 * g.random(self.shape)
-        else:
+            phi0 = W.gaussian_phi0(self.nx, self.ny, max(self.nx, self.ny) / 8.0)
+            if self.bg:
+                phi0 = phi0 + 0.2 + 0.1 * g.random(self.shape)
+        elif self.bg:
             phi0 = 0.5 + g.random(self.shape)
+        else:
+            z, y, x = np.meshgrid(np.arange(self.nz) - self.nz / 2, np.arange(self.ny) - self.ny / 2,
+                                  np.arange(self.nx) - self.nx / 2, indexing="ij")
+            r = max(self.nx, self.ny, self.nz) / 6.0
+            phi0 = np.exp(-(x * x + y * y + z * z) / (2 * r * r))
         phi0 = phi0.astype(np.float32)
         a = None
         if self.ukind == "field":
             a = g.uniform(-self.umax, self.umax, (self.dim,) + self.shape).astype(np.float32)
             if self.bc[0] != "periodic":
                 a[1] *= 0.2      # keep wall-normal flow small near walls
+            if self.bc_x[0] != "periodic":
+                a[0] *= 0.2
+            if self.bc_z[0] != "periodic":
+                a[2] *= 0.2
         elif self.ukind == "row":
             y = np.arange(self.ny, dtype=np.float64)
             W_ = self.ny - 1
@@ -81,7 +95,9 @@ class Case:
 def oracle_params(O, case: Case):
     kw = dict(nx=case.nx, ny=case.ny, nz=case.nz,
               bc_lo=BC_ORACLE[case.bc[0]], bc_hi=BC_ORACLE[case.bc[1]],
-              phi_w_lo=case.phi_w[0], phi_w_hi=case.phi_w[1])
+              phi_w_lo=case.phi_w[0], phi_w_hi=case.phi_w[1],
+              bcx_lo=BC_ORACLE[case.bc_x[0]], bcx_hi=BC_ORACLE[case.bc_x[1]],
+              bcz_lo=BC_ORACLE[case.bc_z[0]], bcz_hi=BC_ORACLE[case.bc_z[1]])
     if case.lattice == 9:
         model = {"A": O.MRT_A, "B1": O.MRT_B1, "B2": O.MRT_B2, "B3": O.MRT_B3}[case.model]
         return O.Params(A=O.A_from_D(case.D), model=model, **kw)
@@ -104,7 +120,8 @@ def run_gpu(case: Case, phi0, a, sched, steps=None, solver_kw=None):
 
     steps = case.steps if steps is None else steps
     s = Solver(lattice=case.lattice, nx=case.nx, ny=case.ny, nz=case.nz, storage=case.storage,
-               bc=case.bc, phi_w=case.phi_w, model=case.model, **(solver_kw or {}))
+               bc=case.bc, phi_w=case.phi_w, model=case.model, bc_x=case.bc_x, bc_z=case.bc_z,
+               **(solver_kw or {}))
     s.set_D(case.D)
     if a is not None:
         s.set_velocity(torch.from_numpy(a).cuda(), None if sched is None else torch.from_numpy(sched).cuda(),
@@ -117,3 +134,15 @@ def run_gpu(case: Case, phi0, a, sched, steps=None, solver_kw=None):
 
 def rel_l2(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def rel_max(a, b):
+    """max |a - b| over max |b|: a per-element bound that a background cannot dilute."""
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def assert_parity(got, want, tol, what=""):
+    """Relative L2 and per-element (max |error| over max |phi|) bounds, both at tol."""
+    e2, em = rel_l2(got, want), rel_max(got, want)
+    assert e2 <= tol and em <= tol, (what, e2, em, tol)
+    return e2, em
