@@ -176,13 +176,13 @@ def replica_totals(seconds, units, world):
     return float(t.item()), float(u.item())
 
 
-def make_solver(store: str):
+def make_solver(store: str, tau: float = TAU):
     import torch
 
     from paper_1404_2363_gb300 import workloads as W
     from paper_1404_2363_gb300.solver import Solver
 
-    wl = W.vortex_workload(N_GRID, TAU)
+    wl = W.vortex_workload(N_GRID, tau)
     s = Solver(nx=N_GRID, ny=N_GRID, storage=store)
     s.set_D(wl["D"])
     a = torch.from_numpy(wl["a"].astype(np.float32)).cuda()
@@ -213,6 +213,16 @@ def time_steps(s, steps, warmup, label=None):
         torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / 1e3
+
+
+def roll(s, seconds: float, chunk: int = 100):
+    """Untimed steps of the solver for at least `seconds` of wall time."""
+    import torch
+
+    t0 = time.time()
+    while time.time() - t0 < seconds:
+        s.step(chunk)
+        torch.cuda.synchronize()
 
 
 def parity_sample(O, store: str, nsteps: int = 24, half: int = 40, npts: int = 6):
@@ -410,21 +420,40 @@ def batch_bench(steps: int):
     b = Batch(descs, graph_steps=64)
     b.set_phi(phis)
     mode, tile = b.autotune(steps=128)
-    b.set_phi(phis)
-    n = max(64, (min(steps, 2000) // 64) * 64)
-    b.run(64, moments=False)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    b.run(n, moments=True)
-    dt = time.perf_counter() - t0
-    cells = b.ncat
-    b.close()
+    n = max(256, (min(steps, 2000) // 64) * 64)
     peak, kind = peaks()
+    cells = b.ncat
+
+    def timed(nsteps):
+        b.set_phi(phis)
+        b.run(64, moments=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(b.stream)
+        b.run(nsteps, moments=True)
+        e1.record(b.stream)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, e0.elapsed_time(e1) / 1e3
+
+    dt, dt_dev = timed(n)
+    modes = {}
+    for m, tr in (("persistent", 0), ("persistent", 16), ("per_step", 0)):
+        b.config(m, tr)
+        w, d = timed(n)
+        key = m if m == "per_step" else ("persistent_cell_tiles" if tr == 0 else f"persistent_warp_tiles{tr}")
+        modes[key] = {
+            "MLUPS_device": cells * n / d / 1e6, "frac_of_" + kind + "_hbm": cells * 72 / (d / n) / 1e9 / peak}
+    b.close()
     gbs = cells * 72 / (dt / n) / 1e9
+    gbs_dev = cells * 72 / (dt_dev / n) / 1e9
     return {"instances": len(chans), "cells": cells, "steps": n, "MLUPS": cells * n / dt / 1e6,
+            "MLUPS_device": cells * n / dt_dev / 1e6,
             "bytes_per_lu": 72, "achieved_gbs": gbs, f"frac_of_{kind}_hbm": gbs / peak,
-            "mode": mode, "tile_rows": tile,
-            "timing": "host wall clock around lbm_cde_batch_run (graph replays + per-step moment copies)"}
+            f"frac_of_{kind}_hbm_device": gbs_dev / peak,
+            "mode": mode, "tile_rows": tile, "modes": modes,
+            "timing": "MLUPS: host wall clock around lbm_cde_batch_run (graph replays + per-step moment "
+                      "copies); MLUPS_device: CUDA events on the batch's stream around the same call"}
 
 
 def adjoint_cost(store: str, ms_forward: float, nsteps: int = 400):
@@ -465,8 +494,10 @@ def inverse_gradient_cost(nsteps: int = 2000, n: int = 1024):
     """The adjoint inverse-problem workload (1024^2 periodic, stream-function
     velocity, 2000 steps): one gradient evaluation of L = sum (phi_N - obs)^2
     with respect to D and phi0 (forward with sqrt(N) checkpoints + reverse
-    sweep), against the plain forward run. At this size the 37 MB state sits in
-    L2, unlike the 4096^2 measurement above."""
+    sweep), against the plain forward run. The torch operations that form
+    dL/dphi_N run once before the timed region, so that loading their kernels
+    (host work on a process's first use) does not leave the GPU idle inside it.
+    The reverse sweep is timed once more with per-phase events."""
     import torch
 
     from paper_1404_2363_gb300 import workloads as W
@@ -477,12 +508,12 @@ def inverse_gradient_cost(nsteps: int = 2000, n: int = 1024):
     s.set_D(wl["D"])
     s.set_velocity(torch.from_numpy(wl["u"].astype(np.float32)).cuda())
     phi0 = torch.from_numpy(wl["phi0"].astype(np.float32)).cuda()
-    obs = phi0.clone()
+    obs = phi0 + 1e-3 * torch.randn(phi0.shape, generator=torch.Generator().manual_seed(5)).cuda()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     s.set_phi(phi0)
     s.step(50)
-    s.forward_ckpt(phi0, nsteps)
-    s.backward(torch.ones_like(phi0))          # warm-up and allocation
+    phiN = s.forward_ckpt(phi0, nsteps)
+    s.backward(2.0 * (phiN - obs))          # warm-up: kernels, buffers, torch ops
     torch.cuda.synchronize()
     ev[0].record(s.stream)
     s.set_phi(phi0)
@@ -493,13 +524,20 @@ def inverse_gradient_cost(nsteps: int = 2000, n: int = 1024):
     s.backward(2.0 * (phiN - obs))
     ev[3].record(s.stream)
     torch.cuda.synchronize()
-    s.close()
     fwd = ev[0].elapsed_time(ev[1])
-    return {"grid": [n, n], "steps": nsteps, "forward_ms": fwd,
-            "forward_ckpt_ms": ev[1].elapsed_time(ev[2]), "backward_ms": ev[2].elapsed_time(ev[3]),
+    bwd = ev[2].elapsed_time(ev[3])
+    s.set_profiling(True)
+    s.backward(2.0 * (phiN - obs))
+    phases = s.backward_phases()
+    s.close()
+    return {"grid": [n, n], "steps": nsteps, "checkpoint_every": int(np.ceil(np.sqrt(nsteps))),
+            "forward_ms": fwd, "forward_ckpt_ms": ev[1].elapsed_time(ev[2]), "backward_ms": bwd,
             "gradient_ms": ev[1].elapsed_time(ev[3]),
+            "ratio_backward_vs_forward": bwd / fwd, "target_ratio_backward_vs_forward": 3.0,
             "ratio_gradient_vs_forward": ev[1].elapsed_time(ev[3]) / fwd,
-            "note": "dL/dD and dL/dphi0 of L = |phi_N - obs|^2; state L2-resident at this size"}
+            "backward_phases_ms": phases,
+            "note": "dL/dD and dL/dphi0 of L = |phi_N - obs|^2 (obs = phi0 + N(0, 1e-3^2)); "
+                    "backward = checkpoint-segment recompute + reverse steps + initial-state term"}
 
 
 def main():
@@ -534,8 +572,16 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(local) as cs:
         time.sleep(0.5)                      # let the sampler start
+        # The K timed steps sit inside about 1.2 s of identical back-to-back
+        # steps (untimed before and after), so that the 100 ms clock sampler
+        # records the clocks the timed steps ran at even when K steps take
+        # only a few milliseconds.
         t_wall0 = time.time()
+        roll(s, 0.6)
+        t_timed0 = time.time()
         dt = time_steps(s, args.steps, args.warmup, label="timed_f32")
+        t_timed1 = time.time()
+        roll(s, 0.6)
         t_wall1 = time.time()
         time.sleep(0.25)
     barrier(world)
@@ -546,19 +592,28 @@ def main():
     avg_launch = dt / args.steps
     peak, peak_kind = peaks()
     achieved = ncell * B_LU[store] / avg_launch / 1e9
+    clocks = cs.summary((t_wall0, t_wall1))
+    clocks["window"] = ("the timed steps inside about 1.2 s of identical untimed steps before and after "
+                        "(samples over that window)")
+    clocks["samples_in_timed_steps"] = cs.summary((t_timed0, t_timed1))["samples"]
+    if clocks["sm_mhz"]:
+        clocks["ms_per_step_x_sm_mhz"] = dt / args.steps * 1e3 * clocks["sm_mhz"]
 
-    # reduced-precision storage forms of the same workload (same timing rules)
+    # reduced-precision storage forms of the same workload, and the workload at
+    # the other two relaxation times tau = 0.6 and 2.0 (same timing rules)
     variants = {}
-    for vs in ("f16", "bf16"):
-        sv, *_ = make_solver(vs)
-        shape = sv.autotune(20)
-        dtv = time_steps(sv, args.steps, args.warmup)
-        sv.close()
-        av = ncell * B_LU[vs] / (dtv / args.steps) / 1e9
-        variants[vs] = {"MLUPS": ncell * args.steps / dtv / 1e6, "bytes_per_lu": B_LU[vs],
-                        "achieved_gbs": av, "frac_of_" + peak_kind + "_hbm": av / peak,
-                        "launch": {"block": shape[0], "vec": shape[1]}}
-    torch.cuda.empty_cache()
+    for tau in (TAU, 0.6, 2.0):
+        for vs in (("f16", "bf16") if tau == TAU else ("f32", "f16", "bf16")):
+            sv, *_ = make_solver(vs, tau)
+            shape = sv.autotune(20)
+            dtv = time_steps(sv, args.steps, args.warmup)
+            sv.close()
+            av = ncell * B_LU[vs] / (dtv / args.steps) / 1e9
+            key = vs if tau == TAU else f"{vs}_tau{tau}"
+            variants[key] = {"MLUPS": ncell * args.steps / dtv / 1e6, "bytes_per_lu": B_LU[vs], "tau": tau,
+                             "achieved_gbs": av, "frac_of_" + peak_kind + "_hbm": av / peak,
+                             "launch": {"block": shape[0], "vec": shape[1]}}
+        torch.cuda.empty_cache()
 
     variants["d3q15_384"] = d3q15_bench(args.steps)
     torch.cuda.empty_cache()
@@ -588,7 +643,7 @@ def main():
                      "kernel": "k_step<D2Q9, F32, FIELD> (one launch per step)",
                      "launch": {"block": f32_shape[0], "vec": f32_shape[1]}},
         "gpu_launches": args.steps,
-        "clocks": cs.summary((t_wall0, t_wall1)),
+        "clocks": clocks,
         "variants": variants,
         "adjoint": adjoint,
         "e2e": e2e,

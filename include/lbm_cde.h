@@ -177,27 +177,29 @@ lbm_status lbm_cde_set_phi(lbm_cde_t h, const float* phi_dev);
 lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps);
 
 /* Sets the launch shape of the step kernel: block threads per CTA along x
- * (a multiple of 32 in [32, 256]) and vec cells per thread (1 or 2; for the
- * D2Q9 16-bit storage forms, 3 selects the row-walking kernel and 4 the
- * shared-memory tile kernel, which needs nx % 32 == 0 and ny % 8 == 0; for
- * the 16-bit storage forms of both lattices, 5 selects the node-pair kernel
+ * (a multiple of 32 in [32, 256]) and vec cells per thread (1 or 2); for the
+ * 16-bit storage forms of both lattices, 5 selects the node-pair kernel
  * (two adjacent nodes per thread in paired FP32 arithmetic), which needs nx
  * even, (q + 3) ncell < 2^31 and an 8-byte aligned velocity field; for D2Q9
  * with any storage, 6 selects the node-quad kernel: four nodes per thread,
  * 128-bit (FP32) or 64-bit (16-bit) vector loads and stores, which needs
  * nx % 4 == 0, 12 ncell < 2^31 and a 16-byte aligned velocity field; for
- * the D2Q9 16-bit storage forms, vec 7 or 8 with block 128 selects the
- * TMA-staged kernel: CTAs walk row ranges of 256-column strips, the source
- * rows arrive in a shared-memory ring through tensor copies (vec 7: two rows
- * per iteration, 256 threads, six stages; vec 8: one row, 128 threads, four
- * stages), which needs nx % 256 == 0, 12 ncell < 2^31 and a 16-byte aligned
- * velocity field; a shape whose field does not meet these runs the one-node
- * kernel).
+ * the 16-bit storage forms, vec 7 or 8 with block 128 selects the TMA-staged
+ * kernel: source rows arrive in a shared-memory ring through tensor copies.
+ * D2Q9: CTAs walk row ranges of 256-column strips (vec 7: two rows per
+ * iteration, 256 threads, six stages; vec 8: one row, 128 threads, four
+ * stages); needs nx % 256 == 0 and 12 ncell < 2^31. D3Q15: CTAs walk row
+ * ranges of a 128-column strip of one z plane, a stage holding one row at the
+ * planes z - 1, z, z + 1 (vec 7: two rows per iteration, 128 threads, five
+ * stages; vec 8: four rows, 256 threads, seven stages); needs nx % 128 == 0
+ * and 18 ncell < 2^31. Both need a 16-byte aligned velocity field. A shape
+ * whose field does not meet these runs the one-node kernel, and so does every
+ * shape when the x or z faces carry walls.
  * Results do not depend on the shape beyond FP32 rounding order. Errors:
  * LBM_E_ARG. */
 lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec);
 
-/* Bound on each device-side wait of the TMA-staged kernel (launch vec 7 / 8), in SM
+/* Bound on each device-side wait of the TMA-staged kernels (launch vec 7 / 8), in SM
  * clock cycles (default 4e9, about 2 s; 0 gives up at once). A wait that runs
  * out latches LBM_E_TIMEOUT, the kernel stops computing, waits (bounded) for
  * its copies in flight and returns; lbm_cde_sum_phi / lbm_cde_sync report the
@@ -206,9 +208,9 @@ lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec);
 lbm_status lbm_cde_set_wait_limit(lbm_cde_t h, int64_t cycles);
 
 /* Autotuner: times every launch shape (block 64/128/256 x vec 1/2, the node-quad
- * kernel for D2Q9, the row-walking, tile, node-pair and TMA-staged kernels for
- * D2Q9 16-bit storage, the node-pair kernel at 64 .. 256 threads for D3Q15
- * 16-bit storage) over `steps` steps from the
+ * kernel for D2Q9, the node-pair and TMA-staged kernels for D2Q9 16-bit
+ * storage, the node-pair kernel at 64 .. 256 threads and the TMA-staged kernel
+ * for D3Q15 16-bit storage) over `steps` steps from the
  * current state, keeps the fastest, and restores the state and step count.
  * With LBMCDE_TUNE_CACHE set, the choice is read from / appended to that text
  * file (lines "key block vec"; the key holds lattice, storage, grid, velocity
@@ -339,12 +341,15 @@ typedef struct {
 
 typedef struct {
     int32_t mode;            /* LBM_BATCH_AUTO (persistent until autotuned) / PERSISTENT (one
-                                cooperative launch per graph chunk, warps walk 32-column row
-                                strips, a bounded grid barrier between steps) / PER_STEP (per
-                                step: one thread per node in 32 x 8 blocks, then two moment
-                                passes) */
-    int32_t tile_rows;       /* PERSISTENT: rows per work tile (a tile is 32 columns x tile_rows
-                                rows, one warp), 1 .. 1024; default 16 */
+                                cooperative launch per graph chunk: blocks or warps take work
+                                tiles from a counter, bounded grid barriers separate the step's
+                                phases) / PER_STEP (per step: one launch over 32 x 16 cell
+                                tiles, two nodes per thread in paired FP32 arithmetic, then two
+                                moment passes) */
+    int32_t tile_rows;       /* PERSISTENT work tiles: 0 (default) the 32 x 16 cell tiles of
+                                PER_STEP taken by whole blocks, with the moment passes between
+                                grid barriers inside the launch; 1 .. 1024: tiles of 32 columns
+                                x tile_rows rows, one warp each, one node per thread */
     int32_t graph_steps;     /* steps per captured CUDA graph (ring of moments), 1 .. 4096 */
     int64_t barrier_timeout_cycles; /* clock64 cycles a CTA waits at a grid barrier before the
                                 launch gives up with LBM_E_TIMEOUT (default 2e9, about 1 s) */
@@ -377,7 +382,7 @@ lbm_status lbm_cde_batch_get_phi(lbm_cde_batch_t b, float* phi_dev);
  * then invalid until the next set_phi). */
 lbm_status lbm_cde_batch_run(lbm_cde_batch_t b, int64_t nsteps, double* moments_host);
 
-/* Times PERSISTENT at tile heights 8, 16, 32 rows and PER_STEP on `steps` steps,
+/* Times PERSISTENT on cell tiles (0) and at tile heights 8, 16, 32 rows, and PER_STEP on `steps` steps,
  * keeps the fastest (restoring the state and step count) and reports it. */
 lbm_status lbm_cde_batch_autotune(lbm_cde_batch_t b, int64_t steps, int32_t* mode_out, int32_t* tile_out);
 

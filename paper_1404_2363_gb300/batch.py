@@ -20,7 +20,7 @@ MODES = {"auto": N.LBM_BATCH_AUTO, "persistent": N.LBM_BATCH_PERSISTENT, "per_st
 
 
 class Batch:
-    def __init__(self, channels, mode="auto", tile_rows=16, graph_steps=64, barrier_timeout_cycles=2_000_000_000,
+    def __init__(self, channels, mode="auto", tile_rows=0, graph_steps=64, barrier_timeout_cycles=2_000_000_000,
                  device=None, stream=None, torch_alloc=True):
         self.L = N.lib()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())

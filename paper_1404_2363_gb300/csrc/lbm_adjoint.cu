@@ -50,15 +50,15 @@ __device__ __forceinline__ void csum_merge(float2& acc, float2 o)
 // Rows handled by one block of the adjoint kernel (AdjArgs::rows): the gradient
 // partials of that many nodes per thread are summed in registers before the
 // block reduction. At most ADJ_ROWS; fewer on small grids, so that the grid
-// still fills the GPU several times over. (A grid of exactly one resident wave,
-// each block walking rows gridDim.y apart, measured slower: 2.99x instead of
-// 2.55x a forward step at 4096^2.)
+// still holds about three resident blocks per SM. (A grid of exactly one
+// resident wave, each block walking rows gridDim.y apart, measured slower:
+// 2.99x instead of 2.55x a forward step at 4096^2.)
 constexpr int ADJ_ROWS = 8;
 
 int adjoint_rows(long long nx, long long ny, long long nz, int sms)
 {
     int rows = ADJ_ROWS;
-    while (rows > 1 && ((nx + 255) / 256) * ((ny + rows - 1) / rows) * nz < (long long)sms * 8) rows /= 2;
+    while (rows > 1 && ((nx + 255) / 256) * ((ny + rows - 1) / rows) * nz < (long long)sms * 3) rows /= 2;
     return rows;
 }
 
@@ -235,20 +235,29 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(con
         }
     }
 
-    // block reduction of the gradient partials (FP32)
+    // block reduction of the gradient partials (FP32), through shared memory:
+    // every thread stores its NG sums as one column of red[NG][256]; then 8 NG
+    // threads add 32 consecutive columns of one row each, and NG threads add the
+    // 8 segments of their row (a fixed order; about a third of the issue slots of
+    // a shuffle tree over NG values)
+    __shared__ float red[NG][256];
+    __shared__ float seg[NG][8];
 #pragma unroll
-    for (int j = 0; j < NG; ++j)
-        for (int off = 16; off > 0; off >>= 1) g[j] += __shfl_down_sync(0xffffffffu, g[j], off);
-    __shared__ float red[8][NG];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0)
-#pragma unroll
-        for (int j = 0; j < NG; ++j) red[warp][j] = g[j];
+    for (int j = 0; j < NG; ++j) red[j][threadIdx.x] = g[j];
+    __syncthreads();
+    if ((int)threadIdx.x < 8 * NG) {
+        const int j = threadIdx.x >> 3, sg = threadIdx.x & 7;
+        const float* r = &red[j][sg * 32];
+        float s = 0.f;
+#pragma unroll 8
+        for (int c = 0; c < 32; ++c) s += r[(c + sg + 8 * j) & 31];   // staggered start: no bank conflicts
+        seg[j][sg] = s;
+    }
     __syncthreads();
     if ((int)threadIdx.x < NG) {
         float s = 0.f;
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+#pragma unroll
+        for (int sg = 0; sg < 8; ++sg) s += seg[threadIdx.x][sg];
         const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
         const long long nb = (long long)gridDim.x * gridDim.y * gridDim.z;
         a.partials[threadIdx.x * nb + blk] = s;   // [NG][nblocks]: coalesced in the reduction

@@ -288,19 +288,15 @@ __global__ void __launch_bounds__(256, 4) k_batch_persistent(const BatchArgs a)
 // rows of one instance). A thread owns the nodes (x, y) and (x, y + 8) and
 // evaluates both collisions in paired FP32 arithmetic (lbm_pair.cuh); warp 0
 // writes the tile's 32 column sums of w_y phi.
+// One 32 x 16 cell tile (tile lt of instance I) of step k: the body of
+// k_batch_cells and of the cell-tile persistent kernel. Block-wide (256
+// threads, one barrier); writes the tile's 32 column sums of w_y phi to strip_out.
 template <typename IX>
-__global__ void __launch_bounds__(256) k_batch_cells(const __grid_constant__ CellArgs a)
+__device__ __forceinline__ void cell_tile(const InstK& I, int lt, long long k, float* const (&buf)[2], long long ncat,
+                                          float* __restrict__ strip_out)
 {
-    const int t = blockIdx.x;
-    int lo = 0, hi = a.ninst - 1;        // instance holding tile t (tile0 ascends)
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.inst[mid].tile0 <= t) lo = mid;
-        else hi = mid - 1;
-    }
-    const InstK& I = a.inst[lo];
     const int nx = I.nx, ny = I.ny;
-    const int lt = t - I.tile0, ty = lt / I.tx;
+    const int ty = lt / I.tx;
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
     const int x = (lt - ty * I.tx) * 32 + lane;
     const int y[2] = {ty * 16 + wy, ty * 16 + 8 + wy};
@@ -308,10 +304,9 @@ __global__ void __launch_bounds__(256) k_batch_cells(const __grid_constant__ Cel
     const bool live[2] = {xlive && y[0] < ny, xlive && y[1] < ny};
     const int xc = min(x, nx - 1);
     const int yc[2] = {min(y[0], ny - 1), min(y[1], ny - 1)};
-    const long long k = *a.kdev + 1;
-    const float* __restrict__ src = a.buf[(k - 1) & 1] + I.off;
-    float* __restrict__ dst = a.buf[k & 1] + I.off;
-    const IX N = (IX)a.ncat;
+    const float* __restrict__ src = buf[(k - 1) & 1] + I.off;
+    float* __restrict__ dst = buf[k & 1] + I.off;
+    const IX N = (IX)ncat;
     const int xs[3] = {xc + 1 == nx ? 0 : xc + 1, xc, xc == 0 ? nx - 1 : xc - 1};
     float f[2][9];
 #pragma unroll
@@ -363,8 +358,23 @@ __global__ void __launch_bounds__(256) k_batch_cells(const __grid_constant__ Cel
         float sum = cs[0][lane];
 #pragma unroll
         for (int r = 1; r < 8; ++r) sum += cs[r][lane];
-        a.strip[(long long)(a.tile_base + t) * 32 + lane] = sum;
+        strip_out[lane] = sum;
     }
+    __syncthreads();   // cs is free again for the block's next tile
+}
+
+template <typename IX>
+__global__ void __launch_bounds__(256) k_batch_cells(const __grid_constant__ CellArgs a)
+{
+    const int t = blockIdx.x;
+    int lo = 0, hi = a.ninst - 1;        // instance holding tile t (tile0 ascends)
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.inst[mid].tile0 <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const InstK& I = a.inst[lo];
+    cell_tile<IX>(I, t - I.tile0, *a.kdev + 1, a.buf, a.ncat, a.strip + (long long)(a.tile_base + t) * 32);
 }
 
 // Eq. 47 moments of step k for PER_STEP mode, two deterministic passes.
@@ -372,14 +382,11 @@ __global__ void __launch_bounds__(256) k_batch_cells(const __grid_constant__ Cel
 // within one instance): phi-bar(x) = FP64 sum of the column's tile sums, then
 // phi-bar {1, xi, xi^2}, reduced over the block in a fixed tree to one partial.
 // Pass 2: one warp per instance adds its block partials in index order.
-__global__ void __launch_bounds__(256) k_batch_col_moments(const BatchArgs a, const float* __restrict__ strip,
-                                                           const int* __restrict__ cblk_inst,
-                                                           double* __restrict__ cpart)
+__device__ __forceinline__ void col_moments(const BatchArgs& a, long long k, int blk, const float* __restrict__ strip,
+                                            const int* __restrict__ cblk_inst, double* __restrict__ cpart)
 {
-    const int blk = blockIdx.x;
     const int i = cblk_inst[blk];
     const InstDev& I = a.inst[i];
-    const long long k = *a.kdev + 1;
     const long long cref = I.xref0 + (long long)llround(I.vref * (double)k);
     const int nx = I.nx;
     const int x = (blk - (int)I.cblk0) * 256 + threadIdx.x;
@@ -407,15 +414,22 @@ __global__ void __launch_bounds__(256) k_batch_col_moments(const BatchArgs a, co
         __syncthreads();
     }
     if (threadIdx.x < 3) cpart[(long long)blk * 3 + threadIdx.x] = r[threadIdx.x][0];
+    __syncthreads();   // r is free again for the block's next column block
 }
 
-__global__ void __launch_bounds__(256) k_batch_inst_moments(const BatchArgs a, const double* __restrict__ cpart)
+__global__ void __launch_bounds__(256) k_batch_col_moments(const BatchArgs a, const float* __restrict__ strip,
+                                                           const int* __restrict__ cblk_inst,
+                                                           double* __restrict__ cpart)
+{
+    col_moments(a, *a.kdev + 1, blockIdx.x, strip, cblk_inst, cpart);
+}
+
+// Pass 2 for instance i (one warp): block partials added in index order with a
+// fixed lane assignment and shuffle tree, written to ring slot (k - 1) mod ring.
+__device__ __forceinline__ void inst_moments(const BatchArgs& a, long long k, int i, const double* __restrict__ cpart)
 {
     const int lane = threadIdx.x & 31;
-    const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    if (i >= a.ninst) return;
     const InstDev& I = a.inst[i];
-    const long long k = *a.kdev + 1;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     for (long long b = I.cblk0 + lane; b < I.cblk0 + I.ncblk; b += 32) {
         s0 += cpart[b * 3 + 0];
@@ -433,6 +447,55 @@ __global__ void __launch_bounds__(256) k_batch_inst_moments(const BatchArgs a, c
         out[0] = s0;
         out[1] = s1;
         out[2] = s2;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_batch_inst_moments(const BatchArgs a, const double* __restrict__ cpart)
+{
+    const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    if (i >= a.ninst) return;
+    inst_moments(a, *a.kdev + 1, i, cpart);
+}
+
+// PERSISTENT mode on cell tiles (tile height 0): one cooperative launch runs
+// the steps of a chunk; each step, the blocks walk the 32 x 16 cell tiles and
+// run the PER_STEP arithmetic (two nodes per thread, paired FP32),
+// then - separated by bounded grid barriers - the column-moment pass over the
+// 256-column blocks and the per-instance sums, as the PER_STEP launches do.
+// The instance constants travel by value in the kernel parameters, as for
+// k_batch_cells (so at most CELL_INST instances), and every read of them is
+// uniform over a block.
+struct PersistArgs {
+    BatchArgs b;
+    const int* tile_inst; // instance of every cell tile
+    int nctiles;          // cell tiles in all
+    float* strip;
+    const int* cblk_inst;
+    int ncblk;
+    double* cpart;
+    int ninst;
+    InstK inst[CELL_INST];   // tile0 = the instance's first cell tile
+};
+
+template <typename IX>
+__global__ void __launch_bounds__(256, 5) k_batch_persistent_cells(const __grid_constant__ PersistArgs p)
+{
+    const BatchArgs& a = p.b;
+    const long long t0 = *a.kdev;
+    for (int s = 0; s < a.nsteps; ++s) {
+        const long long k = t0 + 1 + s;
+        // cell tiles blockIdx.x, blockIdx.x + gridDim.x, ...: equal tiles, so the
+        // static split is even to one tile, and no block waits on a counter
+        for (int t = blockIdx.x; t < p.nctiles; t += gridDim.x) {
+            const InstK& I = p.inst[p.tile_inst[t]];
+            cell_tile<IX>(I, t - I.tile0, k, a.buf, a.ncat, p.strip + (long long)t * 32);
+        }
+        if (!grid_barrier(a)) return;
+        for (int blk = blockIdx.x; blk < p.ncblk; blk += gridDim.x) col_moments(a, k, blk, p.strip, p.cblk_inst, p.cpart);
+        if (!grid_barrier(a)) return;
+        const int gw = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+        const int nw = (int)(((long long)gridDim.x * blockDim.x) >> 5);
+        for (int i = gw; i < a.ninst; i += nw) inst_moments(a, k, i, p.cpart);
     }
 }
 
@@ -473,24 +536,52 @@ __global__ void k_batch_phi(const float* __restrict__ f, long long ncat, float* 
     }
 }
 
-static cudaError_t launch_mode(int mode, const BatchArgs& a, int grid_persistent, long long* kdev,
-                               const std::vector<CellArgs>& cells, const std::vector<int>& cell_tiles,
-                               const float* strip, const int* cblk_inst, int ncblk, double* cpart,
-                               cudaStream_t st)
+static int occupancy_grid(const void* fn)
 {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 256, 0);
+    return std::max(1, per) * sms;
+}
+
+// rows > 0: PERSISTENT on warp tiles of that height; rows == 0: on cell tiles
+static cudaError_t launch_mode(int mode, int rows, const BatchArgs& a, const InstK* cinst, const int* tile_inst,
+                               int ninst, long long* kdev,
+                               const std::vector<CellArgs>& cells, const std::vector<int>& cell_tiles, int nctiles,
+                               float* strip, const int* cblk_inst, int ncblk, double* cpart, cudaStream_t st)
+{
+    // 32-bit offsets when the last plane offset 9 ncat fits in 31 bits
+    const bool i32 = 9LL * a.ncat < (1LL << 31);
     if (mode == LBM_BATCH_PERSISTENT) {
         // tile counters start at zero for the first step of the launch
         cudaError_t e = cudaMemsetAsync(a.counter, 0, 2 * sizeof(unsigned), st);
         if (e != cudaSuccess) return e;
-        void* args[] = {(void*)&a};
-        e = cudaLaunchCooperativeKernel((const void*)k_batch_persistent, dim3(grid_persistent), dim3(256), args,
-                                        0, st);
+        if (rows > 0) {
+            void* args[] = {(void*)&a};
+            e = cudaLaunchCooperativeKernel((const void*)k_batch_persistent,
+                                            dim3(occupancy_grid((const void*)k_batch_persistent)), dim3(256), args,
+                                            0, st);
+        } else {
+            PersistArgs p{};
+            p.b = a;
+            p.tile_inst = tile_inst;
+            p.nctiles = nctiles;
+            p.strip = strip;
+            p.cblk_inst = cblk_inst;
+            p.ncblk = ncblk;
+            p.cpart = cpart;
+            p.ninst = ninst;
+            for (int i = 0; i < ninst; ++i) p.inst[i] = cinst[i];
+            void* args[] = {(void*)&p};
+            const void* fn = i32 ? (const void*)k_batch_persistent_cells<int>
+                                 : (const void*)k_batch_persistent_cells<long long>;
+            e = cudaLaunchCooperativeKernel(fn, dim3(occupancy_grid(fn)), dim3(256), args, 0, st);
+        }
         if (e != cudaSuccess) return e;
         k_batch_advance<<<1, 1, 0, st>>>(kdev, a.nsteps);
         return cudaGetLastError();
     }
-    // 32-bit offsets when the last plane offset 9 ncat fits in 31 bits
-    const bool i32 = 9LL * a.ncat < (1LL << 31);
     for (int s = 0; s < a.nsteps; ++s) {
         for (size_t g = 0; g < cells.size(); ++g) {
             if (i32) k_batch_cells<int><<<(unsigned)cell_tiles[g], 256, 0, st>>>(cells[g]);
@@ -501,15 +592,6 @@ static cudaError_t launch_mode(int mode, const BatchArgs& a, int grid_persistent
         k_batch_advance<<<1, 1, 0, st>>>(kdev, 1);
     }
     return cudaGetLastError();
-}
-
-static int persistent_grid()
-{
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_persistent, 256, 0);
-    return std::max(1, per) * sms;
 }
 
 }  // namespace lbm
@@ -534,13 +616,16 @@ struct lbm_cde_batch_s {
     long long t = 0;
     bool ready = false;
     int mode = LBM_BATCH_PERSISTENT;
-    int rows = 16;                 // rows per warp tile
+    int rows = 0;                  // rows per warp tile (PERSISTENT); 0: the cell tiles
     int chunk = 64;                // steps per graph replay
     cudaGraphExec_t graph = nullptr;   // one chunk of steps, built lazily for (mode, rows)
     int graph_key[2] = {-1, -1};
     bool use_graph = true;
     double* stage = nullptr;       // pinned host staging for one chunk of moments
     std::vector<lbm::CellArgs> cells;   // PER_STEP launches (instances in groups of CELL_INST)
+    std::vector<lbm::InstK> cinst;      // every instance's constants (cell-tile PERSISTENT mode)
+    int* tile_inst = nullptr;           // instance of every cell tile (cell-tile PERSISTENT mode)
+    int nctiles = 0;                    // cell tiles in all
     std::vector<int> cell_tiles;        // cell tiles of each launch
     float* strip = nullptr;             // [cell tiles][32] column sums
     int* cblk_inst = nullptr;           // instance of each 256-column block of the moment pass
@@ -644,8 +729,9 @@ static lbm::BatchArgs batch_args(lbm_cde_batch_t b, int nsteps)
 
 static cudaError_t launch_batch(lbm_cde_batch_t b, const lbm::BatchArgs& a)
 {
-    return lbm::launch_mode(b->mode, a, lbm::persistent_grid(), b->kdev, b->cells, b->cell_tiles, b->strip,
-                            b->cblk_inst, b->ncblk, b->cpart, b->st);
+    return lbm::launch_mode(b->mode, b->rows, a, b->cinst.data(), b->tile_inst, b->n, b->kdev, b->cells, b->cell_tiles,
+                            b->nctiles,
+                            b->strip, b->cblk_inst, b->ncblk, b->cpart, b->st);
 }
 
 static void drop_graph(lbm_cde_batch_t b)
@@ -690,14 +776,15 @@ static lbm_status ensure_graph(lbm_cde_batch_t b)
     return LBM_OK;
 }
 
-// Warp tiles: 32 columns x a strip of at most b->rows rows.
+// Warp tiles: 32 columns x a strip of at most b->rows rows (none for rows == 0,
+// the cell tiles of the PER_STEP arithmetic).
 static lbm_status rebuild_tiles(lbm_cde_batch_t b)
 {
     b->tiles.clear();
     for (int i = 0; i < b->n; ++i) {
         b->inst[i].tile0 = (long long)b->tiles.size();
         const int ny = b->inst[i].ny;
-        const int nstrip = (ny + b->rows - 1) / b->rows;
+        const int nstrip = b->rows > 0 ? (ny + b->rows - 1) / b->rows : 0;
         for (int sidx = 0; sidx < nstrip; ++sidx) {
             // strips of nearly equal height
             const int y0 = (int)((long long)ny * sidx / nstrip);
@@ -708,11 +795,12 @@ static lbm_status rebuild_tiles(lbm_cde_batch_t b)
     }
     bfree(b, b->tiles_dev);
     bfree(b, b->partials);
-    b->tiles_dev = static_cast<lbm::TileDev*>(balloc(b, sizeof(lbm::TileDev) * b->tiles.size()));
-    b->partials = static_cast<double*>(balloc(b, sizeof(double) * 6 * b->tiles.size()));
+    b->tiles_dev = static_cast<lbm::TileDev*>(balloc(b, sizeof(lbm::TileDev) * std::max<size_t>(1, b->tiles.size())));
+    b->partials = static_cast<double*>(balloc(b, sizeof(double) * 6 * std::max<size_t>(1, b->tiles.size())));
     if (!b->tiles_dev || !b->partials) return bfail(b, LBM_E_OOM, "tile allocation failed");
-    BCK(b, cudaMemcpyAsync(b->tiles_dev, b->tiles.data(), sizeof(lbm::TileDev) * b->tiles.size(),
-                           cudaMemcpyHostToDevice, b->st));
+    if (!b->tiles.empty())
+        BCK(b, cudaMemcpyAsync(b->tiles_dev, b->tiles.data(), sizeof(lbm::TileDev) * b->tiles.size(),
+                               cudaMemcpyHostToDevice, b->st));
     BCK(b, cudaMemcpyAsync(b->inst_dev, b->inst.data(), sizeof(lbm::InstDev) * b->n, cudaMemcpyHostToDevice,
                            b->st));
     BCK(b, cudaStreamSynchronize(b->st));
@@ -727,7 +815,7 @@ lbm_status lbm_cde_batch_opts_init(lbm_cde_batch_opts* o)
     if (!o) return bfail(nullptr, LBM_E_ARG, "NULL opts");
     std::memset(o, 0, sizeof(*o));
     o->mode = LBM_BATCH_AUTO;
-    o->tile_rows = 16;
+    o->tile_rows = 0;
     o->graph_steps = 64;
     o->barrier_timeout_cycles = 2000000000LL;
     return LBM_OK;
@@ -742,7 +830,7 @@ lbm_status lbm_cde_batch_create(const lbm_cde_channel_desc* descs, int32_t n, co
     if (opts) o = *opts;
     else lbm_cde_batch_opts_init(&o);
     if ((o.alloc == nullptr) != (o.free_ == nullptr)) return bfail(nullptr, LBM_E_ARG, "alloc/free_ mismatch");
-    if (o.tile_rows < 1 || o.tile_rows > 1024) return bfail(nullptr, LBM_E_ARG, "tile_rows in [1, 1024]");
+    if (o.tile_rows < 0 || o.tile_rows > 1024) return bfail(nullptr, LBM_E_ARG, "tile_rows in [0, 1024]");
     if (o.graph_steps < 1 || o.graph_steps > 4096) return bfail(nullptr, LBM_E_ARG, "graph_steps in [1, 4096]");
     if (o.barrier_timeout_cycles < 0) return bfail(nullptr, LBM_E_ARG, "negative barrier timeout");
     lbm_cde_batch_t b = new (std::nothrow) lbm_cde_batch_s();
@@ -750,7 +838,7 @@ lbm_status lbm_cde_batch_create(const lbm_cde_channel_desc* descs, int32_t n, co
     b->o = o;
     b->n = n;
     b->st = static_cast<cudaStream_t>(o.stream);
-    b->rows = o.tile_rows;
+    b->rows = o.tile_rows == 0 && n > lbm::CELL_INST ? 16 : o.tile_rows;   // cell tiles: <= CELL_INST instances
     b->chunk = o.graph_steps;
     b->mode = o.mode == LBM_BATCH_PER_STEP ? LBM_BATCH_PER_STEP : LBM_BATCH_PERSISTENT;
     b->inst.resize(n);
@@ -865,6 +953,28 @@ lbm_status lbm_cde_batch_create(const lbm_cde_channel_desc* descs, int32_t n, co
         b->cells.push_back(ca);
         b->cell_tiles.push_back((int)tiles);
     }
+    {
+        // the same constants for every instance in one device array, tile0 global
+        std::vector<lbm::InstK> all((size_t)n);
+        for (size_t g = 0; g < b->cells.size(); ++g)
+            for (int j = 0; j < b->cells[g].ninst; ++j) {
+                lbm::InstK K = b->cells[g].inst[j];
+                K.tile0 += b->cells[g].tile_base;
+                all[g * lbm::CELL_INST + j] = K;
+            }
+        b->nctiles = (int)ncell_tiles;
+        std::vector<int> ti((size_t)ncell_tiles);
+        for (int i = 0; i < n; ++i)
+            for (long long q = 0; q < (long long)b->inst[i].tx * b->inst[i].tyc; ++q) ti[(size_t)(b->inst[i].ctile0 + q)] = i;
+        b->cinst = all;
+        b->tile_inst = static_cast<int*>(balloc(b, sizeof(int) * ti.size()));
+        if (!b->tile_inst) {
+            lbm_cde_batch_destroy(b);
+            return bfail(nullptr, LBM_E_OOM, "batch allocation failed");
+        }
+        cudaMemcpyAsync(b->tile_inst, ti.data(), sizeof(int) * ti.size(), cudaMemcpyHostToDevice, b->st);
+        cudaStreamSynchronize(b->st);
+    }
     cudaMemsetAsync(b->sync, 0, 64, b->st);
     lbm_status s = rebuild_tiles(b);
     if (s != LBM_OK) {
@@ -891,6 +1001,7 @@ lbm_status lbm_cde_batch_destroy(lbm_cde_batch_t b)
     bfree(b, b->strip);
     bfree(b, b->cblk_inst);
     bfree(b, b->cpart);
+    bfree(b, b->tile_inst);
     delete b;
     return LBM_OK;
 }
@@ -981,7 +1092,7 @@ lbm_status lbm_cde_batch_autotune(lbm_cde_batch_t b, int64_t steps, int32_t* mod
     BCK(b, cudaMemcpyAsync(save, b->buf[b->t & 1], sb, cudaMemcpyDeviceToDevice, b->st));
     const long long t_save = b->t;
     const int modes[2] = {LBM_BATCH_PERSISTENT, LBM_BATCH_PER_STEP};
-    const int tws[3] = {8, 16, 32};
+    const int tws[4] = {0, 8, 16, 32};
     float best = 1e30f;
     int best_mode = b->mode, best_tw = b->rows;
     cudaEvent_t e0, e1;
@@ -990,6 +1101,7 @@ lbm_status lbm_cde_batch_autotune(lbm_cde_batch_t b, int64_t steps, int32_t* mod
     for (int m : modes)
         for (int tw : tws) {
             if (m == LBM_BATCH_PER_STEP && tw != tws[0]) continue;   // fixed 32 x 16 cell tiles
+            if (m == LBM_BATCH_PERSISTENT && tw == 0 && b->n > lbm::CELL_INST) continue;
             b->mode = m;
             if (b->rows != tw) {
                 b->rows = tw;
@@ -1032,9 +1144,10 @@ lbm_status lbm_cde_batch_autotune(lbm_cde_batch_t b, int64_t steps, int32_t* mod
 
 lbm_status lbm_cde_batch_config(lbm_cde_batch_t b, int32_t mode, int32_t tile_rows)
 {
-    if (!b || (mode != LBM_BATCH_PERSISTENT && mode != LBM_BATCH_PER_STEP) || tile_rows < 1 || tile_rows > 1024)
+    if (!b || (mode != LBM_BATCH_PERSISTENT && mode != LBM_BATCH_PER_STEP) || tile_rows < 0 || tile_rows > 1024)
         return bfail(b, LBM_E_ARG, "bad mode or tile height");
     b->mode = mode;
+    if (tile_rows == 0 && b->n > lbm::CELL_INST) tile_rows = 16;   // cell tiles: <= CELL_INST instances
     if (b->rows != tile_rows) {
         b->rows = tile_rows;
         return rebuild_tiles(b);

@@ -46,8 +46,11 @@ struct lbm_cde_s {
     // adjoint: checkpoints of the forward run, segment recompute buffer, adjoint states
     std::vector<void*> ck;
     int64_t ck_every = 0, ck_nsteps = 0;
-    void* seg = nullptr;
+    void* seg = nullptr;           // recomputed states of a checkpoint segment
+    void* seg2 = nullptr;          // second segment buffer (overlapped reverse sweep), or NULL
     int64_t seg_states = 0;
+    cudaStream_t st_rec = nullptr; // stream of the segment recompute in the overlapped sweep
+    cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_adj[2] = {nullptr, nullptr}, ev_start = nullptr;
     float* mu[2] = {nullptr, nullptr};
     float* adj_partials = nullptr;
     float2* grad_acc = nullptr;
@@ -423,6 +426,7 @@ lbm_status lbm_cde_destroy(lbm_cde_t h)
 {
     if (!h) return LBM_OK;
     cudaStreamSynchronize(h->st);
+    if (h->st_rec) cudaStreamSynchronize(h->st_rec);
     for (int b = 0; b < 2; ++b) {
         dev_free(h, h->state[b]);
         dev_free(h, h->phi[b]);
@@ -431,6 +435,13 @@ lbm_status lbm_cde_destroy(lbm_cde_t h)
     dev_free(h, h->partials);
     for (void* p : h->ck) dev_free(h, p);
     dev_free(h, h->seg);
+    dev_free(h, h->seg2);
+    for (int p = 0; p < 2; ++p) {
+        if (h->ev_rec[p]) cudaEventDestroy(h->ev_rec[p]);
+        if (h->ev_adj[p]) cudaEventDestroy(h->ev_adj[p]);
+    }
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->st_rec) cudaStreamDestroy(h->st_rec);
     dev_free(h, h->mu[0]);
     dev_free(h, h->mu[1]);
     dev_free(h, h->adj_partials);
@@ -536,7 +547,6 @@ lbm_status lbm_cde_set_wait_limit(lbm_cde_t h, int64_t cycles)
 lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec)
 {
     if (!h) return fail(h, LBM_E_ARG, "NULL handle");
-    const bool tile_ok = h->d.nx % 32 == 0 && h->d.ny % 8 == 0;
     const bool pair_ok = h->neq && h->d.nx % 2 == 0 && (long long)(h->q + 3) * h->ncell < (1LL << 31);
     const bool quad = h->q == 9 && h->d.nx % 4 == 0 && 12LL * h->ncell < (1LL << 31);
     const bool tma = h->neq && ((h->q == 9 && h->d.nx % 256 == 0 && 12LL * h->ncell < (1LL << 31)) ||
@@ -549,13 +559,11 @@ lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec)
         h->cfg.vec = vec;
         return LBM_OK;
     }
-    if (block < 32 || block > 256 || block % 32 != 0 || vec < 1 || vec > 6 ||
-        (vec >= 3 && vec <= 4 && !(h->q == 9 && h->neq)) || (vec == 4 && !tile_ok) || (vec == 5 && !pair_ok) ||
-        (vec == 6 && !quad))
-        return fail(h, LBM_E_ARG, "block must be a multiple of 32 in [32, 256]; vec 1 or 2 "
-                                  "(3: row-walking kernel, 4: shared-memory tile kernel with nx % 32 == 0 "
-                                  "and ny % 8 == 0, both D2Q9 16-bit storage only; 5: node-pair kernel "
-                                  "with nx even, 16-bit storage; 6: D2Q9 node-quad kernel with nx % 4 == 0)");
+    if (block < 32 || block > 256 || block % 32 != 0 || vec < 1 || vec > 6 || vec == 3 || vec == 4 ||
+        (vec == 5 && !pair_ok) || (vec == 6 && !quad))
+        return fail(h, LBM_E_ARG, "block must be a multiple of 32 in [32, 256]; vec 1 or 2 (one or two nodes "
+                                  "per thread), 5 (node-pair kernel, nx even, 16-bit storage) or 6 (D2Q9 "
+                                  "node-quad kernel, nx % 4 == 0)");
     h->cfg.block = block;
     h->cfg.vec = vec;
     return LBM_OK;
@@ -640,18 +648,14 @@ lbm_status lbm_cde_autotune(lbm_cde_t h, int64_t steps, int32_t* block_out, int3
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     // candidates: generic kernel (1 or 2 nodes per thread) at 64/128/256 threads;
-    // for D2Q9 16-bit storage also the row-walking and tile kernels (one shape
-    // each) and the node-pair kernel at 64/128/256 threads; for D3Q15 16-bit
-    // storage the node-pair kernel at 64 .. 256 threads
+    // for D2Q9 16-bit storage also the node-pair kernel at 64/128/256 threads; for
+    // D3Q15 16-bit storage the node-pair kernel at 64 .. 256 threads; the node-quad
+    // kernel (D2Q9) and the TMA-staged kernels (16-bit storage) where they apply
     std::vector<LaunchCfg> cand;
     for (int vec = 1; vec <= 2; ++vec)
         for (int b : {64, 128, 256}) cand.push_back(LaunchCfg{b, vec});
-    if (h->q == 9 && h->neq) {
-        cand.push_back(LaunchCfg{256, 3});
-        if (h->d.nx % 32 == 0 && h->d.ny % 8 == 0) cand.push_back(LaunchCfg{256, 4});
-        if (h->d.nx % 2 == 0 && 12LL * h->ncell < (1LL << 31))
-            for (int b : {64, 128, 256}) cand.push_back(LaunchCfg{b, 5});
-    }
+    if (h->q == 9 && h->neq && h->d.nx % 2 == 0 && 12LL * h->ncell < (1LL << 31))
+        for (int b : {64, 128, 256}) cand.push_back(LaunchCfg{b, 5});
     if (h->q == 15 && h->neq && h->d.nx % 2 == 0 && 18LL * h->ncell < (1LL << 31))
         for (int b : {64, 96, 128, 192, 256}) cand.push_back(LaunchCfg{b, 5});
     if (h->q == 9 && h->d.nx % 4 == 0 && 12LL * h->ncell < (1LL << 31))
@@ -931,8 +935,13 @@ lbm_status lbm_cde_forward_ckpt(lbm_cde_t h, const float* phi0_dev, int64_t nste
     const int64_t segn = every > 1 ? every - 1 : 1;
     if (h->seg_states != segn) {
         dev_free(h, h->seg);
+        dev_free(h, h->seg2);
         h->seg = dev_alloc(h, sb * segn);
         if (!h->seg) return fail(h, LBM_E_OOM, "segment allocation failed");
+        // a second segment buffer lets the reverse sweep recompute the next
+        // segment while it runs the adjoint steps of this one; without it the
+        // sweep runs the two one after the other
+        h->seg2 = nck > 1 ? dev_alloc(h, sb * segn) : nullptr;
         h->seg_states = segn;
     }
     if (!h->phi0_saved) {
@@ -978,13 +987,15 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
     // and after its reverse steps (lbm_cde_set_profiling)
     struct Events {
         std::vector<cudaEvent_t> e;
+        std::vector<int> kind;   // 0: recompute boundary, 1: reverse-step boundary, 2: sweep
         ~Events() { for (cudaEvent_t x : e) cudaEventDestroy(x); }
-        cudaError_t mark(cudaStream_t st)
+        cudaError_t mark(cudaStream_t st, int k = 2)
         {
             cudaEvent_t x = nullptr;
             cudaError_t r = cudaEventCreate(&x);
             if (r != cudaSuccess) return r;
             e.push_back(x);
+            kind.push_back(k);
             return cudaEventRecord(x, st);
         }
     } ev;
@@ -997,23 +1008,72 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
     int cur = 0;
     const int64_t K = h->ck_every, Nst = h->ck_nsteps;
     const int64_t nck = (int64_t)h->ck.size();
+    // Overlapped sweep (two segment buffers): segment j's states sit in buffer
+    // j & 1; the recompute of segment j - 1 runs on st_rec while the adjoint steps
+    // of segment j run on the handle's stream, ordered by events (a buffer is
+    // refilled only after the adjoint steps that read it). Otherwise the
+    // recompute and the adjoint steps of each segment run in turn.
+    bool overlap = h->seg2 != nullptr;
+    if (overlap && !h->st_rec) {
+        if (cudaStreamCreateWithFlags(&h->st_rec, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            h->st_rec = nullptr;
+        } else {
+            bool ok = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming) == cudaSuccess;
+            for (int p = 0; p < 2 && ok; ++p)
+                ok = cudaEventCreateWithFlags(&h->ev_rec[p], cudaEventDisableTiming) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&h->ev_adj[p], cudaEventDisableTiming) == cudaSuccess;
+            if (!ok) return fail(h, LBM_E_CUDA, "event creation failed");
+        }
+    }
+    overlap = overlap && h->st_rec != nullptr;
+    void* segbuf[2] = {h->seg, overlap ? h->seg2 : h->seg};
     auto seg_state = [&](int64_t j, int64_t t) -> float* {   // B_{jK + t}
         if (t == 0) return static_cast<float*>(h->ck[j]);
-        return reinterpret_cast<float*>(static_cast<char*>(h->seg) + sb * (t - 1));
+        return reinterpret_cast<float*>(static_cast<char*>(segbuf[j & 1]) + sb * (t - 1));
     };
-    for (int64_t j = nck - 1; j >= 0; --j) {
-        const int64_t start = j * K;
-        const int64_t end = std::min(start + K, Nst);
-        if (h->prof) CK(h, ev.mark(h->st));
-        // recompute B_{start+1} .. B_{end-1} from the checkpoint
+    // recompute B_{jK+1} .. B_{end-1} of segment j from its checkpoint, on stream rs
+    auto recompute = [&](int64_t j, cudaStream_t rs) -> lbm_status {
+        const int64_t start = j * K, end = std::min(start + K, Nst);
         for (int64_t t = 1; t < end - start; ++t) {
             StepArgs a = make_args(h, 0);
             a.src = seg_state(j, t - 1);
             a.dst = seg_state(j, t);
             set_step(a, start + t);
-            CK(h, lbm::launch_step(h->q, LBM_STORE_F32, uk, walls, h->cfg, a, h->st));
+            CK(h, lbm::launch_step(h->q, LBM_STORE_F32, uk, walls, h->cfg, a, rs));
         }
-        if (h->prof) CK(h, ev.mark(h->st));
+        return LBM_OK;
+    };
+    if (overlap) {
+        CK(h, cudaEventRecord(h->ev_start, h->st));   // checkpoints and seed are ordered before
+        CK(h, cudaStreamWaitEvent(h->st_rec, h->ev_start, 0));
+        if (h->prof) CK(h, ev.mark(h->st_rec, 0));
+        s = recompute(nck - 1, h->st_rec);
+        if (s != LBM_OK) return s;
+        if (h->prof) CK(h, ev.mark(h->st_rec, 0));
+        CK(h, cudaEventRecord(h->ev_rec[(nck - 1) & 1], h->st_rec));
+    }
+    for (int64_t j = nck - 1; j >= 0; --j) {
+        const int64_t start = j * K;
+        const int64_t end = std::min(start + K, Nst);
+        if (overlap) {
+            CK(h, cudaStreamWaitEvent(h->st, h->ev_rec[j & 1], 0));
+            if (j >= 1) {
+                // buffer (j - 1) & 1 was last read by the adjoint steps of segment j + 1
+                if (j + 1 < nck) CK(h, cudaStreamWaitEvent(h->st_rec, h->ev_adj[(j + 1) & 1], 0));
+                if (h->prof) CK(h, ev.mark(h->st_rec, 0));
+                s = recompute(j - 1, h->st_rec);
+                if (s != LBM_OK) return s;
+                if (h->prof) CK(h, ev.mark(h->st_rec, 0));
+                CK(h, cudaEventRecord(h->ev_rec[(j - 1) & 1], h->st_rec));
+            }
+        } else {
+            if (h->prof) CK(h, ev.mark(h->st, 0));
+            s = recompute(j, h->st);
+            if (s != LBM_OK) return s;
+            if (h->prof) CK(h, ev.mark(h->st, 0));
+        }
+        if (h->prof) CK(h, ev.mark(h->st, 1));
         for (int64_t k = end; k > start; --k) {
             lbm::AdjArgs a = make_adj(h, k, h->mu[cur], h->mu[1 - cur], seg_state(j, k - 1 - start), dL_da_dev,
                                       h->grad_acc);
@@ -1025,7 +1085,8 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
             }
             cur ^= 1;
         }
-        if (h->prof) CK(h, ev.mark(h->st));
+        if (h->prof) CK(h, ev.mark(h->st, 1));
+        if (overlap) CK(h, cudaEventRecord(h->ev_adj[j & 1], h->st));
     }
     lbm::AdjArgs a0 = make_adj(h, 0, h->mu[cur], nullptr, nullptr, dL_da_dev, h->grad_acc);
     if (nslice > 0) CK(h, lbm::launch_grad_reduce(h->q, a0, h->adj_partials, nslice, slice, h->st));
@@ -1035,21 +1096,20 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
     if (h->prof) CK(h, ev.mark(h->st));
     CK(h, cudaStreamSynchronize(h->st));
     if (h->prof) {
-        // events: start, then (before recompute, before reverse steps, after) per segment, end
-        double rec = 0.0, adj = 0.0, tot = 0.0;
+        // events: the first and the last mark the whole sweep on the handle's
+        // stream; in between, pairs (before, after) of one segment's recompute and
+        // of one segment's reverse steps, in the order they were issued
+        double rec = 0.0, adj = 0.0;
         float ms = 0.f;
         const size_t ne = ev.e.size();
-        for (size_t j = 1; j + 2 < ne; j += 3) {
+        for (size_t j = 1; j + 2 < ne; j += 2) {
             CK(h, cudaEventElapsedTime(&ms, ev.e[j], ev.e[j + 1]));
-            rec += ms;
-            CK(h, cudaEventElapsedTime(&ms, ev.e[j + 1], ev.e[j + 2]));
-            adj += ms;
+            (ev.kind[j] ? adj : rec) += ms;
         }
         CK(h, cudaEventElapsedTime(&ms, ev.e[0], ev.e[ne - 1]));
-        tot = ms;
         h->prof_ms[0] = rec;
         h->prof_ms[1] = adj;
-        h->prof_ms[2] = tot;
+        h->prof_ms[2] = ms;
     }
     double g[33];
     for (int j = 0; j < ng; ++j) g[j] = (double)gc[j].x + (double)gc[j].y;   // compensated sum, host FP64

@@ -678,317 +678,6 @@ __global__ void __launch_bounds__(256) k_step_box(const StepArgs a)
     if (NEQ) a.phi_dst[cell] = phi;
 }
 
-// ---------------------------------------------------------------------------
-// D2Q9 step for the 16-bit offset storage. The decode
-//     f_i = g_i(s_i) + w_i phi(s_i) + k_i e_i . (phi u)(s_i),   s_i = x - e_i,
-// needs phi and phi u(k-1) at all nine pull sources. A thread owns one column
-// and walks NEQ_ROWS rows; it keeps (phi, phi u_x, phi u_y) of rows y-1, y, y+1
-// for columns x-1, x, x+1 in registers, loading only the new row y+2 of its own
-// column per step and taking the neighbour columns from the adjacent lanes by
-// shuffles (direct loads only at warp edges and at the periodic seam).
-// ---------------------------------------------------------------------------
-constexpr int NEQ_ROWS = 16;
-
-struct RowVals {
-    float p, jx, jy;    // phi, phi u_x(k-1), phi u_y(k-1) at the source column
-};
-
-template <int UK>
-__device__ __forceinline__ RowVals neq_row_vals(const StepArgs& a, int r, int col, const float* sp,
-                                                float& axr, float& ayr)
-{
-    const long long c = (long long)r * a.nx + col;
-    RowVals v;
-    v.p = __ldg(a.phi_src + c);
-    axr = ayr = 0.f;
-    if (UK == U_FIELD) {
-        axr = __ldg(a.ua + c);
-        ayr = __ldg(a.ua + a.ncell + c);
-    } else if (UK == U_ROW) {
-        axr = __ldg(a.ua + r);
-        ayr = __ldg(a.ua + a.ny + r);
-    }
-    v.jx = v.p * (axr * sp[0]);
-    v.jy = v.p * (ayr * sp[1]);
-    return v;
-}
-
-template <int STORE, int UK, bool WALLS>
-__global__ void __launch_bounds__(256) k_step_neq_d2q9(const StepArgs a)
-{
-    using T = typename StT<STORE>::T;
-    using L = D2Q9;
-    const int nx = a.nx, ny = a.ny;
-    const long long N = a.ncell;
-    const T* __restrict__ src = static_cast<const T*>(a.src);
-    T* __restrict__ dst = static_cast<T*>(a.dst);
-    const int lane = threadIdx.x & 31;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = x < nx;
-    const int xc = live ? x : nx - 1;
-    const int xm = xc == 0 ? nx - 1 : xc - 1;
-    const int xp = xc == nx - 1 ? 0 : xc + 1;
-    const bool needL = lane == 0 || xc == 0;
-    const bool needR = lane == 31 || xc == nx - 1;
-    const Coef& c = a.c;
-    float s_now[3], s_prev[3];
-    sched_row_at(a.sched, a.srow_now, 2, s_now);
-    sched_row_at(a.sched, a.srow_prev, 2, s_prev);
-
-    // window: [row][column], row 0 = y-1, 1 = y, 2 = y+1; column 0 = x-1, 1 = x, 2 = x+1
-    RowVals W[3][3];
-    float AX[3], AY[3];   // raw velocity factors of the own column (for u(k) and walls)
-    const int y0 = blockIdx.y * NEQ_ROWS;
-    auto load_row = [&](int slot, int r) {
-        float axr, ayr, dx, dy;
-        RowVals v = neq_row_vals<UK>(a, r, xc, s_prev, axr, ayr);
-        AX[slot] = axr;
-        AY[slot] = ayr;
-        RowVals l, rr;
-        l.p = __shfl_up_sync(0xffffffffu, v.p, 1);
-        l.jx = __shfl_up_sync(0xffffffffu, v.jx, 1);
-        l.jy = __shfl_up_sync(0xffffffffu, v.jy, 1);
-        rr.p = __shfl_down_sync(0xffffffffu, v.p, 1);
-        rr.jx = __shfl_down_sync(0xffffffffu, v.jx, 1);
-        rr.jy = __shfl_down_sync(0xffffffffu, v.jy, 1);
-        if (needL) l = neq_row_vals<UK>(a, r, xm, s_prev, dx, dy);
-        if (needR) rr = neq_row_vals<UK>(a, r, xp, s_prev, dx, dy);
-        W[slot][0] = l;
-        W[slot][1] = v;
-        W[slot][2] = rr;
-    };
-    load_row(0, y0 == 0 ? ny - 1 : y0 - 1);
-    load_row(1, y0);
-    load_row(2, y0 + 1 == ny ? 0 : y0 + 1);
-    const int xs[3] = {xp, xc, xm};   // source column by e_x + 1
-
-    // software pipeline: the stored offsets of row y+1 and the own-column
-    // values of row y+2 are requested before row y is computed
-    auto load_g = [&](int y, float* g) {
-        const int ys[3] = {y + 1 == ny ? 0 : y + 1, y, y == 0 ? ny - 1 : y - 1};
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-            g[i] = ldg_f(src + (long long)i * N + (long long)ys[L::ey(i) + 1] * nx + xs[L::ex(i) + 1]);
-    };
-    float gc[9], gn[9];
-    load_g(y0, gc);
-
-    for (int yy = 0; yy < NEQ_ROWS; ++yy) {
-        const int y = y0 + yy;
-        if (y >= ny) break;
-        const bool more = yy + 1 < NEQ_ROWS && y + 1 < ny;
-        RowVals nv;
-        float nax = 0.f, nay = 0.f;
-        if (more) {
-            load_g(y + 1, gn);
-            nv = neq_row_vals<UK>(a, y + 2 >= ny ? y + 2 - ny : y + 2, xc, s_prev, nax, nay);
-        }
-        float f[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const RowVals& v = W[1 - L::ey(i)][1 - L::ex(i)];
-            const int w = wclass<L>(i);
-            const float wi = w == 0 ? c.w0 : (w == 1 ? c.wa : c.wd);
-            const float ki = w == 1 ? c.ka : c.kd;
-            const float ej = (float)L::ex(i) * v.jx + (float)L::ey(i) * v.jy;
-            f[i] = (w == 0) ? fmaf(wi, v.p, gc[i]) : fmaf(ki, ej, fmaf(wi, v.p, gc[i]));
-        }
-        const long long cell = (long long)y * nx + xc;
-        if (WALLS) {
-            const bool lo = (y == 0) && a.bc_lo != BC_PERIODIC;
-            const bool hi = (y == ny - 1) && a.bc_hi != BC_PERIODIC;
-            if (lo || hi) {
-                const int kind = lo ? a.bc_lo : a.bc_hi;
-                const int inward = lo ? 1 : -1;
-                if (kind == BC_NOFLUX) {
-#pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        if (L::ey(i) == inward) f[i] = f[mirror_y<L>(i)];
-                } else if (kind == BC_BOUNCE) {
-                    const RowVals& v = W[1][1];
-#pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        if (L::ey(i) == inward) {
-                            const int o = opposite<L>(i);
-                            const int w = wclass<L>(o);
-                            const float wi = w == 1 ? c.wa : c.wd;
-                            const float ki = w == 1 ? c.ka : c.kd;
-                            const float ej = (float)L::ex(o) * v.jx + (float)L::ey(o) * v.jy;
-                            f[i] = fmaf(ki, ej, fmaf(wi, v.p, ldg_f(src + (long long)o * N + cell)));
-                        }
-                } else {
-                    const float ux = AX[1] * s_prev[0], uy = AY[1] * s_prev[1];
-                    float known = 0.f, wk = 0.f;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        if (L::ey(i) == inward) wk += feq_unit<L>(c, i, ux, uy, 0.f);
-                        else known += f[i];
-                    }
-                    const float ps = ((lo ? a.phiw_lo : a.phiw_hi) - known) / wk;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        if (L::ey(i) == inward) f[i] = ps * feq_unit<L>(c, i, ux, uy, 0.f);
-                }
-            }
-        }
-        const float ux = AX[1] * s_now[0], uy = AY[1] * s_now[1];
-        const float phi = collide<L, true>(f, ux, uy, 0.f, c);
-        if (live) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) st_f(dst + (long long)i * N + cell, f[i]);
-            a.phi_dst[cell] = phi;
-        }
-        if (more) {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                W[0][j] = W[1][j];
-                W[1][j] = W[2][j];
-            }
-            AX[0] = AX[1];
-            AY[0] = AY[1];
-            AX[1] = AX[2];
-            AY[1] = AY[2];
-            AX[2] = nax;
-            AY[2] = nay;
-            const int r = y + 2 >= ny ? y + 2 - ny : y + 2;
-            RowVals l, rr;
-            float dx, dy;
-            l.p = __shfl_up_sync(0xffffffffu, nv.p, 1);
-            l.jx = __shfl_up_sync(0xffffffffu, nv.jx, 1);
-            l.jy = __shfl_up_sync(0xffffffffu, nv.jy, 1);
-            rr.p = __shfl_down_sync(0xffffffffu, nv.p, 1);
-            rr.jx = __shfl_down_sync(0xffffffffu, nv.jx, 1);
-            rr.jy = __shfl_down_sync(0xffffffffu, nv.jy, 1);
-            if (needL) l = neq_row_vals<UK>(a, r, xm, s_prev, dx, dy);
-            if (needR) rr = neq_row_vals<UK>(a, r, xp, s_prev, dx, dy);
-            W[2][0] = l;
-            W[2][1] = nv;
-            W[2][2] = rr;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) gc[i] = gn[i];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// D2Q9 16-bit step with a shared-memory tile: a 32 x 8 block stages
-// (phi, phi u_x(k-1), phi u_y(k-1)) of its nodes plus a one-node halo, so each
-// node loads three own values instead of the 27 values of its nine sources.
-// Needs nx % 32 == 0 and ny % 8 == 0 (the halo indices assume whole tiles).
-// ---------------------------------------------------------------------------
-template <int UK>
-__device__ __forceinline__ void neq_stage(const StepArgs& a, int r, int col, const float* sp, float* P,
-                                          float* JX, float* JY, int slot)
-{
-    float axr, ayr;
-    const RowVals v = neq_row_vals<UK>(a, r, col, sp, axr, ayr);
-    P[slot] = v.p;
-    JX[slot] = v.jx;
-    JY[slot] = v.jy;
-}
-
-template <int STORE, int UK, bool WALLS>
-__global__ void __launch_bounds__(256) k_step_neq_tile_d2q9(const StepArgs a)
-{
-    using T = typename StT<STORE>::T;
-    using L = D2Q9;
-    constexpr int BX = 32, BY = 8, SW = BX + 2;
-    const int nx = a.nx, ny = a.ny;
-    const int N = (int)a.ncell;
-    const T* __restrict__ src = static_cast<const T*>(a.src);
-    T* __restrict__ dst = static_cast<T*>(a.dst);
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-    const int x = x0 + tx, y = y0 + ty;
-    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-    const Coef& c = a.c;
-    float s_now[3], s_prev[3];
-    sched_row_at(a.sched, a.srow_now, 2, s_now);
-    sched_row_at(a.sched, a.srow_prev, 2, s_prev);
-
-    __shared__ float P[(BY + 2) * SW], JX[(BY + 2) * SW], JY[(BY + 2) * SW];
-    float axo, ayo;   // own raw velocity factors
-    {
-        const RowVals v = neq_row_vals<UK>(a, y, x, s_prev, axo, ayo);
-        const int o = (ty + 1) * SW + tx + 1;
-        P[o] = v.p;
-        JX[o] = v.jx;
-        JY[o] = v.jy;
-    }
-    if (ty == 0) neq_stage<UK>(a, ym, x, s_prev, P, JX, JY, tx + 1);
-    if (ty == BY - 1) neq_stage<UK>(a, yp, x, s_prev, P, JX, JY, (BY + 1) * SW + tx + 1);
-    if (tx == 0) {
-        neq_stage<UK>(a, y, xm, s_prev, P, JX, JY, (ty + 1) * SW);
-        if (ty == 0) neq_stage<UK>(a, ym, xm, s_prev, P, JX, JY, 0);
-        if (ty == BY - 1) neq_stage<UK>(a, yp, xm, s_prev, P, JX, JY, (BY + 1) * SW);
-    }
-    if (tx == BX - 1) {
-        neq_stage<UK>(a, y, xp, s_prev, P, JX, JY, (ty + 1) * SW + BX + 1);
-        if (ty == 0) neq_stage<UK>(a, ym, xp, s_prev, P, JX, JY, BX + 1);
-        if (ty == BY - 1) neq_stage<UK>(a, yp, xp, s_prev, P, JX, JY, (BY + 1) * SW + BX + 1);
-    }
-    __syncthreads();
-
-    const int xs[3] = {xp, x, xm};   // source column by e_x + 1
-    const int ys[3] = {yp, y, ym};   // source row by e_y + 1
-    float f[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int sl = (ty + 1 - L::ey(i)) * SW + tx + 1 - L::ex(i);
-        const float g = ldg_f(src + i * N + ys[L::ey(i) + 1] * nx + xs[L::ex(i) + 1]);
-        const int w = wclass<L>(i);
-        const float wi = w == 0 ? c.w0 : (w == 1 ? c.wa : c.wd);
-        const float ki = w == 1 ? c.ka : c.kd;
-        const float ej = (float)L::ex(i) * JX[sl] + (float)L::ey(i) * JY[sl];
-        f[i] = (w == 0) ? fmaf(wi, P[sl], g) : fmaf(ki, ej, fmaf(wi, P[sl], g));
-    }
-    const int cell = y * nx + x;
-    if (WALLS) {
-        const bool lo = (y == 0) && a.bc_lo != BC_PERIODIC;
-        const bool hi = (y == ny - 1) && a.bc_hi != BC_PERIODIC;
-        if (lo || hi) {
-            const int kind = lo ? a.bc_lo : a.bc_hi;
-            const int inward = lo ? 1 : -1;
-            const int so = (ty + 1) * SW + tx + 1;
-            if (kind == BC_NOFLUX) {
-#pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    if (L::ey(i) == inward) f[i] = f[mirror_y<L>(i)];
-            } else if (kind == BC_BOUNCE) {
-#pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    if (L::ey(i) == inward) {
-                        const int o = opposite<L>(i);
-                        const int w = wclass<L>(o);
-                        const float wi = w == 1 ? c.wa : c.wd;
-                        const float ki = w == 1 ? c.ka : c.kd;
-                        const float ej = (float)L::ex(o) * JX[so] + (float)L::ey(o) * JY[so];
-                        f[i] = fmaf(ki, ej, fmaf(wi, P[so], ldg_f(src + o * N + cell)));
-                    }
-            } else {
-                const float ux = axo * s_prev[0], uy = ayo * s_prev[1];
-                float known = 0.f, wk = 0.f;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    if (L::ey(i) == inward) wk += feq_unit<L>(c, i, ux, uy, 0.f);
-                    else known += f[i];
-                }
-                const float ps = ((lo ? a.phiw_lo : a.phiw_hi) - known) / wk;
-#pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    if (L::ey(i) == inward) f[i] = ps * feq_unit<L>(c, i, ux, uy, 0.f);
-            }
-        }
-    }
-    const float ux = axo * s_now[0], uy = ayo * s_now[1];
-    const float phi = collide<L, true>(f, ux, uy, 0.f, c);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) st_f(dst + i * N + cell, f[i]);
-    a.phi_dst[cell] = phi;
-}
-
-// f = f^eq(phi0, u(0)) (F32) or g = 0, phi = phi0 (16-bit forms)
 template <class L, int STORE, int UK>
 __global__ void k_init(const StepArgs a, const float* __restrict__ phi0)
 {

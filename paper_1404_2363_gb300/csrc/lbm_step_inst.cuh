@@ -51,18 +51,6 @@ static cudaError_t step_vec(LaunchCfg cfg, const StepArgs& a, cudaStream_t st)
             k_step_pair_d2q9<STORE, UK, WALLS><<<grid, cfg.block, 0, st>>>(a);
             return cudaGetLastError();
         }
-        if (cfg.vec == 4 && a.nx % 32 == 0 && a.ny % 8 == 0 && 12LL * a.ncell < (1LL << 31)) {
-            // shared-memory tile variant of the offset storage (32 x 8 blocks)
-            dim3 grid((unsigned)(a.nx / 32), (unsigned)(a.ny / 8), 1);
-            k_step_neq_tile_d2q9<STORE, UK, WALLS><<<grid, 256, 0, st>>>(a);
-            return cudaGetLastError();
-        }
-        if (cfg.vec == 3) {
-            // row-walking variant of the offset storage (fixed 256-thread shape)
-            dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)((a.ny + NEQ_ROWS - 1) / NEQ_ROWS), 1);
-            k_step_neq_d2q9<STORE, UK, WALLS><<<grid, 256, 0, st>>>(a);
-            return cudaGetLastError();
-        }
     }
     const int vec = cfg.vec == 2 ? 2 : 1;
     const int per = cfg.block * vec;

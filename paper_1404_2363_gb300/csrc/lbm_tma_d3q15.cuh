@@ -307,8 +307,9 @@ __global__ void __launch_bounds__(T3_TP * TR)
     (void)nxp;
 }
 
-// strips x planes x row ranges: as many row ranges per (strip, plane) as one
-// wave of resident CTAs allows (at least one)
+// strips x planes x row ranges: the number of row ranges per (strip, plane)
+// minimises the waves of resident CTAs times the rows one CTA stages (its range
+// plus the two rows around it), so that the last wave is not left nearly empty
 template <int STORE, int UK, bool WALLS, int R, int NS>
 cudaError_t launch_tma_d3q15(const StepArgs& a, cudaStream_t st)
 {
@@ -327,8 +328,17 @@ cudaError_t launch_tma_d3q15(const StepArgs& a, cudaStream_t st)
         resident = (nsm > 0 ? nsm : 1) * (per_sm > 0 ? per_sm : 1);
     }
     const int nstrip = a.nx / T3_W;
-    long long nb = resident / ((long long)nstrip * a.nz);
-    nb = nb < 1 ? 1 : (nb > a.ny ? a.ny : nb);
+    long long nb = 1;
+    double best = 1e300;
+    for (long long b = 1; b <= 64 && b <= a.ny; ++b) {
+        const long long ctas = (long long)nstrip * a.nz * b;
+        const double waves = (double)((ctas + resident - 1) / resident);
+        const double cost = waves * (double)((a.ny + b - 1) / b + 2);
+        if (cost < best * 0.999) {
+            best = cost;
+            nb = b;
+        }
+    }
     k_step_tma_d3q15<STORE, UK, WALLS, R, NS>
         <<<dim3((unsigned)nstrip, (unsigned)a.nz, (unsigned)nb), threads, smem, st>>>(a, *a.tma15);
     return cudaGetLastError();

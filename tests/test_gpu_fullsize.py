@@ -181,8 +181,8 @@ def test_vortex_5000_steps_error_vs_fp64(O, storage, tol, launch, tau):
     assert mass <= {"f32": 1e-6, "f16": 1e-5 if tau < 2 else 1e-4, "bf16": 2e-4 if tau < 2 else 5e-4}[storage]
 
 
-@pytest.mark.parametrize("mode", ["per_step", "persistent"])
-def test_taylor_aris_batch_64_windows(O, mode):
+@pytest.mark.parametrize("mode,tile", [("per_step", 8), ("persistent", 8), ("persistent", 0)])
+def test_taylor_aris_batch_64_windows(O, mode, tile):
     """The 64-channel Taylor-Aris workload of bench.py at full size, in both batch
     modes: column windows of three channels (all rows, walls included) run by the
     oracle as channels of their own are exact on their central columns."""
@@ -197,7 +197,7 @@ def test_taylor_aris_batch_64_windows(O, mode):
                       "x_ref0": 0.2 * c.nx, "x_ref_velocity": mean_velocity(u)})
         phis.append(c.phi0().astype(np.float32) + 0.05)
     nsteps, half = 20, 30
-    b = Batch(descs, mode=mode, tile_rows=8, graph_steps=16)
+    b = Batch(descs, mode=mode, tile_rows=tile, graph_steps=16)
     b.set_phi(phis)
     b.run(nsteps, moments=False)
     got = [g.cpu().numpy().astype(np.float64) for g in b.get_phi()]
