@@ -215,6 +215,29 @@ def time_steps(s, steps, warmup, label=None):
     return e0.elapsed_time(e1) / 1e3
 
 
+def copy_rate_same_size(nbytes: int, reps: int = 20):
+    """Read + write GB/s of a device-to-device copy of nbytes (torch copy_),
+    best of reps: the copy peak at the size of one step's state, beside the
+    driver's 2 GiB figure in the denominator."""
+    import torch
+
+    a = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    b.copy_(a)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    torch.cuda.empty_cache()
+    return 2 * nbytes / best / 1e9
+
+
 def roll(s, seconds: float, chunk: int = 100):
     """Untimed steps of the solver for at least `seconds` of wall time."""
     import torch
@@ -247,6 +270,7 @@ def parity_sample(O, store: str, nsteps: int = 24, half: int = 40, npts: int = 6
     n = 2 * half + 1
     keep = half - nsteps - 1
     num = den = 0.0
+    emax = wmax = 0.0
     for (x0, y0) in pts:
         ix = (np.arange(x0 - half, x0 + half + 1)) % N_GRID
         iy = (np.arange(y0 - half, y0 + half + 1)) % N_GRID
@@ -258,7 +282,10 @@ def parity_sample(O, store: str, nsteps: int = 24, half: int = 40, npts: int = 6
         gw = got[np.ix_(iy, ix)][half - keep:half + keep + 1, half - keep:half + keep + 1]
         num += float(((gw - want) ** 2).sum())
         den += float((want ** 2).sum())
-    return float(np.sqrt(num / den)), f"{npts} windows of {2 * keep + 1}^2 cells after {nsteps} steps"
+        emax = max(emax, float(np.abs(gw - want).max()))
+        wmax = max(wmax, float(np.abs(want).max()))
+    return (float(np.sqrt(num / den)), emax / wmax,
+            f"{npts} windows of {2 * keep + 1}^2 cells after {nsteps} steps")
 
 
 def cpu_baseline(O, max_seconds: float = 20.0):
@@ -599,6 +626,8 @@ def main():
     if clocks["sm_mhz"]:
         clocks["ms_per_step_x_sm_mhz"] = dt / args.steps * 1e3 * clocks["sm_mhz"]
 
+    copy_same = copy_rate_same_size(ncell * 36)   # one FP32 state buffer (9 planes)
+
     # reduced-precision storage forms of the same workload, and the workload at
     # the other two relaxation times tau = 0.6 and 2.0 (same timing rules)
     variants = {}
@@ -640,6 +669,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profile_traffic(store),
                      "peak_source": peak_kind, "bytes_per_lu": B_LU[store],
+                     "copy_gbs_same_size": copy_same,
                      "kernel": "k_step<D2Q9, F32, FIELD> (one launch per step)",
                      "launch": {"block": f32_shape[0], "vec": f32_shape[1]}},
         "gpu_launches": args.steps,
@@ -653,8 +683,9 @@ def main():
         import oracle as O
 
         O.build()
-        err, sample = parity_sample(O, store)
-        out["parity"] = {"phi_rel_l2_vs_fp64": err, "sample": sample, "tolerance": 1e-5}
+        err, emax, sample = parity_sample(O, store)
+        out["parity"] = {"phi_rel_l2_vs_fp64": err, "phi_max_err_over_max_phi": emax, "sample": sample,
+                         "tolerance": 1e-5}
         out["cpu_baseline"] = cpu_baseline(O)
     print(json.dumps(out), flush=True)
     barrier(world)
