@@ -184,22 +184,25 @@ lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps);
  * with any storage, 6 selects the node-quad kernel: four nodes per thread,
  * 128-bit (FP32) or 64-bit (16-bit) vector loads and stores, which needs
  * nx % 4 == 0, 12 ncell < 2^31 and a 16-byte aligned velocity field; for
- * the 16-bit storage forms, vec 7 or 8 with block 128 selects the TMA-staged
- * kernel: source rows arrive in a shared-memory ring through tensor copies.
- * D2Q9: CTAs walk row ranges of 256-column strips (vec 7: two rows per
+ * D2Q9 16-bit storage, vec 7 or 8 with block 128 selects the TMA-staged
+ * kernel: source rows arrive in a shared-memory ring through tensor copies,
+ * CTAs walking row ranges of 256-column strips (vec 7: two rows per
  * iteration, 256 threads, six stages; vec 8: one row, 128 threads, four
- * stages); needs nx % 256 == 0 and 12 ncell < 2^31. D3Q15: CTAs walk row
- * ranges of a 128-column strip of one z plane, a stage holding one row at the
- * planes z - 1, z, z + 1 (vec 7: two rows per iteration, 128 threads, five
- * stages; vec 8: four rows, 256 threads, seven stages); needs nx % 128 == 0
- * and 18 ncell < 2^31. Both need a 16-byte aligned velocity field. A shape
+ * stages); needs nx % 256 == 0, 12 ncell < 2^31 and a 16-byte aligned
+ * velocity field. For D3Q15 16-bit storage, vec 9 with block 256 or 128
+ * selects the z-walk kernel: CTAs own 64 x (block / 32) tiles of the (x, y)
+ * plane and walk a range of z planes, with phi and the velocity factors of the
+ * planes z - 1 .. z + 1 and the offsets each step pulls staged in shared
+ * memory by asynchronous copies; needs nx % 64 == 0, ny a multiple of
+ * block / 32, 18 ncell < 2^31 and 16-byte aligned offsets, phi and velocity
+ * fields. A shape
  * whose field does not meet these runs the one-node kernel, and so does every
  * shape when the x or z faces carry walls.
  * Results do not depend on the shape beyond FP32 rounding order. Errors:
  * LBM_E_ARG. */
 lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec);
 
-/* Bound on each device-side wait of the TMA-staged kernels (launch vec 7 / 8), in SM
+/* Bound on each device-side wait of the TMA-staged D2Q9 kernel (launch vec 7 / 8), in SM
  * clock cycles (default 4e9, about 2 s; 0 gives up at once). A wait that runs
  * out latches LBM_E_TIMEOUT, the kernel stops computing, waits (bounded) for
  * its copies in flight and returns; lbm_cde_sum_phi / lbm_cde_sync report the
@@ -207,9 +210,16 @@ lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec);
  * (cycles < 0). */
 lbm_status lbm_cde_set_wait_limit(lbm_cde_t h, int64_t cycles);
 
+/* Planes each CTA of the D3Q15 z-walk kernel (launch vec 9) walks: 0 (the
+ * default) lets the launcher choose the z ranges so that the resident CTAs
+ * fill whole waves; planes > 0 splits nz into ceil(nz / planes) ranges of
+ * nearly equal length. Results do not depend on it. Errors: LBM_E_ARG
+ * (planes < 0). */
+lbm_status lbm_cde_set_zwalk(lbm_cde_t h, int32_t planes);
+
 /* Autotuner: times every launch shape (block 64/128/256 x vec 1/2, the node-quad
  * kernel for D2Q9, the node-pair and TMA-staged kernels for D2Q9 16-bit
- * storage, the node-pair kernel at 64 .. 256 threads and the TMA-staged kernel
+ * storage, the node-pair kernel at 64 .. 256 threads and the z-walk kernel
  * for D3Q15 16-bit storage) over `steps` steps from the
  * current state, keeps the fastest, and restores the state and step count.
  * With LBMCDE_TUNE_CACHE set, the choice is read from / appended to that text

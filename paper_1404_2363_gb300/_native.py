@@ -110,6 +110,7 @@ SIGNATURES = {
     "lbm_cde_step": [_P, _I64],
     "lbm_cde_set_launch": [_P, ctypes.c_int32, ctypes.c_int32],
     "lbm_cde_set_wait_limit": [_P, _I64],
+    "lbm_cde_set_zwalk": [_P, ctypes.c_int32],
     "lbm_cde_autotune": [_P, _I64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "lbm_cde_get_time": [_P, ctypes.POINTER(_I64)],
     "lbm_cde_get_phi": [_P, _P],

@@ -59,11 +59,11 @@ struct lbm_cde_s {
     // TMA-staged D2Q9 step (launch vec 7): tensor maps per source buffer, and the
     // device status word its bounded waits report to
     lbm::TmaMaps tmaps[2];
-    lbm::TmaMaps15 tmaps15[2];
     bool tmaps_ok = false;
     const float* tmaps_ua = nullptr;
     int* status_dev = nullptr;
     long long wait_limit = 4000000000LL;   // SM cycles per bounded device wait (about 2 s)
+    int zwalk = 0;                         // z-walk kernel: planes per CTA (0: automatic)
     int sms = 152;                         // multiprocessors of the device (adjoint grid)
     // per-phase device time of the last backward sweep (lbm_cde_set_profiling)
     bool prof = false;
@@ -211,6 +211,7 @@ static void refresh_coef(lbm_cde_t h)
         c.wd = (float)(1.0 / 15.0 + 5.0 * a1 / 108.0 + a2 / 8640.0);
         c.ka = (float)(1.0 / 5.0);
         c.kd = (float)(3.0 / 40.0);
+        lbm::fold_offset_coef(c, 15);
     }
     const double na = h->q == 9 ? 4.0 : 6.0, nd = h->q == 9 ? 4.0 : 8.0;
     c.eps0 = (float)((double)c.w0 + na * (double)c.wa + nd * (double)c.wd - 1.0);
@@ -242,6 +243,7 @@ static StepArgs make_args(lbm_cde_t h, int src_idx)
     a.c = h->coef;
     a.status = h->status_dev;
     a.spin_limit = h->wait_limit;
+    a.zwalk = h->zwalk;
     return a;
 }
 
@@ -252,10 +254,7 @@ static lbm_status ensure_tma_maps(lbm_cde_t h)
     if (h->tmaps_ok && h->tmaps_ua == ua) return LBM_OK;
     h->tmaps_ok = false;
     for (int b = 0; b < 2; ++b) {
-        const bool ok = h->q == 9 ? lbm::encode_tma_maps(h->state[b], h->phi[b], ua, (int)h->d.nx, (int)h->d.ny,
-                                                         &h->tmaps[b])
-                                  : lbm::encode_tma_maps15(h->state[b], h->phi[b], ua, (int)h->d.nx, (int)h->d.ny,
-                                                           (int)h->d.nz, &h->tmaps15[b]);
+        const bool ok = lbm::encode_tma_maps(h->state[b], h->phi[b], ua, (int)h->d.nx, (int)h->d.ny, &h->tmaps[b]);
         if (!ok) return fail(h, LBM_E_CUDA, "tensor map encoding failed (launch vec 7 / 8)");
     }
     h->tmaps_ok = true;
@@ -521,15 +520,14 @@ lbm_status lbm_cde_step(lbm_cde_t h, int64_t nsteps)
     if (!h->ready) return fail(h, LBM_E_STATE, "set_phi must come before step");
     const bool walls = h->d.bc_lo_y != LBM_BC_PERIODIC;
     const int uk = ukind_internal(h->ukind);
-    const bool tma = (h->cfg.vec == 7 || h->cfg.vec == 8) && h->neq;
+    const bool tma = (h->cfg.vec == 7 || h->cfg.vec == 8) && h->neq && h->q == 9;
     if (tma) {
         const lbm_status ts = ensure_tma_maps(h);
         if (ts != LBM_OK) return ts;
     }
     for (int64_t n = 0; n < nsteps; ++n) {
         StepArgs a = make_args(h, h->cur);
-        if (tma && h->q == 9) a.tma = &h->tmaps[h->cur];
-        if (tma && h->q == 15) a.tma15 = &h->tmaps15[h->cur];
+        if (tma) a.tma = &h->tmaps[h->cur];
         CK(h, lbm::launch_step(h->q, h->d.storage, uk, walls, h->cfg, a, h->st));
         h->cur ^= 1;
         h->t += 1;
@@ -544,17 +542,32 @@ lbm_status lbm_cde_set_wait_limit(lbm_cde_t h, int64_t cycles)
     return LBM_OK;
 }
 
+lbm_status lbm_cde_set_zwalk(lbm_cde_t h, int32_t planes)
+{
+    if (!h || planes < 0) return fail(h, LBM_E_ARG, "bad argument");
+    h->zwalk = planes;
+    return LBM_OK;
+}
+
 lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec)
 {
     if (!h) return fail(h, LBM_E_ARG, "NULL handle");
     const bool pair_ok = h->neq && h->d.nx % 2 == 0 && (long long)(h->q + 3) * h->ncell < (1LL << 31);
     const bool quad = h->q == 9 && h->d.nx % 4 == 0 && 12LL * h->ncell < (1LL << 31);
-    const bool tma = h->neq && ((h->q == 9 && h->d.nx % 256 == 0 && 12LL * h->ncell < (1LL << 31)) ||
-                                (h->q == 15 && h->d.nx % 128 == 0 && 18LL * h->ncell < (1LL << 31)));
+    const bool tma = h->neq && h->q == 9 && h->d.nx % 256 == 0 && 12LL * h->ncell < (1LL << 31);
+    if (vec == 9) {
+        if ((block != 256 && block != 128) || !h->neq || h->q != 15 || h->d.nx % 64 != 0 ||
+            h->d.ny % (block / 32) != 0 || 18LL * h->ncell >= (1LL << 31))
+            return fail(h, LBM_E_ARG, "vec 9 (D3Q15 z-walk 16-bit kernel) needs block 256 or 128, nx % 64 == 0 "
+                                      "and ny a multiple of block / 32");
+        h->cfg.block = block;
+        h->cfg.vec = vec;
+        return LBM_OK;
+    }
     if (vec == 7 || vec == 8) {
         if (block != 128 || !tma)
-            return fail(h, LBM_E_ARG, "vec 7 / 8 (TMA-staged 16-bit kernels) needs block 128 and nx % 256 == 0 "
-                                      "(D2Q9) or nx % 128 == 0 (D3Q15)");
+            return fail(h, LBM_E_ARG, "vec 7 / 8 (TMA-staged D2Q9 16-bit kernel) needs block 128 and "
+                                      "nx % 256 == 0");
         h->cfg.block = block;
         h->cfg.vec = vec;
         return LBM_OK;
@@ -650,7 +663,8 @@ lbm_status lbm_cde_autotune(lbm_cde_t h, int64_t steps, int32_t* block_out, int3
     // candidates: generic kernel (1 or 2 nodes per thread) at 64/128/256 threads;
     // for D2Q9 16-bit storage also the node-pair kernel at 64/128/256 threads; for
     // D3Q15 16-bit storage the node-pair kernel at 64 .. 256 threads; the node-quad
-    // kernel (D2Q9) and the TMA-staged kernels (16-bit storage) where they apply
+    // kernel (D2Q9), the TMA-staged D2Q9 kernel (16-bit storage) and the D3Q15
+    // z-walk kernel where they apply
     std::vector<LaunchCfg> cand;
     for (int vec = 1; vec <= 2; ++vec)
         for (int b : {64, 128, 256}) cand.push_back(LaunchCfg{b, vec});
@@ -660,8 +674,10 @@ lbm_status lbm_cde_autotune(lbm_cde_t h, int64_t steps, int32_t* block_out, int3
         for (int b : {64, 96, 128, 192, 256}) cand.push_back(LaunchCfg{b, 5});
     if (h->q == 9 && h->d.nx % 4 == 0 && 12LL * h->ncell < (1LL << 31))
         for (int b : {64, 128, 256}) cand.push_back(LaunchCfg{b, 6});
-    if (h->neq && ((h->q == 9 && h->d.nx % 256 == 0 && 12LL * h->ncell < (1LL << 31)) ||
-                   (h->q == 15 && h->d.nx % 128 == 0 && 18LL * h->ncell < (1LL << 31))) &&
+    if (h->q == 15 && h->neq && h->d.nx % 64 == 0 && 18LL * h->ncell < (1LL << 31))
+        for (int b : {128, 256})
+            if (h->d.ny % (b / 32) == 0) cand.push_back(LaunchCfg{b, 9});
+    if (h->neq && h->q == 9 && h->d.nx % 256 == 0 && 12LL * h->ncell < (1LL << 31) &&
         ensure_tma_maps(h) == LBM_OK) {   // tensor maps available
         cand.push_back(LaunchCfg{128, 7});
         cand.push_back(LaunchCfg{128, 8});

@@ -139,9 +139,31 @@ __device__ __forceinline__ T collide_d3q15(T (&f)[15], T ux, T uy, T uz, const C
 #pragma unroll
     for (int k = 9; k < 15; ++k) dl[k] = m[k];
     // m' = m - S dl with the flux rows 3, 5, 7 coupled to rows 4, 6, 8 (Eq. A.5),
-    // scaled by 1 / |M_k|^2; the offset form keeps m' - m^eq = dl - S dl
-    const T(&base)[15] = OFFSET ? dl : m;
+    // scaled by 1 / |M_k|^2; the offset form keeps m' - m^eq = dl - S dl, with
+    // the relaxation and the scaling folded into c.ro and c.fr
     T a[15];
+    if constexpr (OFFSET) {
+        a[1] = vmul(c.ro[1], dl[1]);
+        a[2] = vmul(c.ro[2], dl[2]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            T r = vmul(c.fr[6 * q], dl[3]);
+            r = vfma(c.fr[6 * q + 1], dl[4], r);
+#pragma unroll
+            for (int b = 1; b < 3; ++b) {
+                r = vfma(c.fr[6 * q + 2 * b], dl[3 + 2 * b], r);
+                r = vfma(c.fr[6 * q + 2 * b + 1], dl[4 + 2 * b], r);
+            }
+            a[3 + 2 * q] = r;
+            a[4 + 2 * q] = vmul(c.ro[4 + 2 * q], dl[4 + 2 * q]);
+        }
+#pragma unroll
+        for (int k = 9; k < 15; ++k) a[k] = vmul(c.ro[k], dl[k]);
+        const T moving = d3q15_populations<T, true, false>(a, f);
+        f[0] = vfma(-c.eps0, phi, vneg(moving));   // rest population from the mass balance
+        return phi;
+    }
+    const T(&base)[15] = m;
     a[0] = vmul(1.0f / (float)row_norm2<D3Q15>(0), phi);   // not read by the offset form
     a[1] = vmul(1.0f / (float)row_norm2<D3Q15>(1), vfma(-c.s[1], dl[1], base[1]));
     a[2] = vmul(1.0f / (float)row_norm2<D3Q15>(2), vfma(-c.s[2], dl[2], base[2]));
@@ -161,10 +183,8 @@ __device__ __forceinline__ T collide_d3q15(T (&f)[15], T ux, T uy, T uz, const C
 #pragma unroll
     for (int k = 9; k < 15; ++k)
         a[k] = vmul(1.0f / (float)row_norm2<D3Q15>(k), vfma(-c.s[k], dl[k], base[k]));
-    const T moving = d3q15_populations<T, OFFSET, false>(a, f);
-    // rest population from the mass balance (see collide in lbm_device.cuh)
-    if constexpr (OFFSET) f[0] = vfma(-c.eps0, phi, vneg(moving));
-    else f[0] = vsub(phi, moving);
+    const T moving = d3q15_populations<T, false, false>(a, f);
+    f[0] = vsub(phi, moving);   // rest population from the mass balance (see collide in lbm_device.cuh)
     return phi;
 }
 

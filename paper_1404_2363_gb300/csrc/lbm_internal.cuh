@@ -31,30 +31,43 @@ struct Coef {
     // u^2 terms of the MRT-B1/B2 equilibria (Eq. 38-39), zero for MRT-A/B3:
     //   m1 += b1 |u|^2 phi, m2 += b2 |u|^2 phi, m7 = g7 (ux^2 - uy^2) phi, m8 = g8 ux uy phi
     float b1, b2, g7, g8;
-    // D2Q9 offset form (linear equilibria): the relaxation and the 1/|M_k|^2
+    // Offset forms (linear equilibria): the relaxation and the 1/|M_k|^2
     // scaling folded together, a_k = (m' - m^eq)_k / |M_k|^2 from dl = m - m^eq:
-    //   ro[k] = (1 - s_k) / |M_k|^2                      (k = 1, 2, 4, 6, 7, 8)
-    //   fr[4 r + j]: flux row 3 + 2 r on dl_3, dl_4, dl_5, dl_6
-    //               ((delta_r0 - A_r0) / 6, -C_r0 / 6, (delta_r1 - A_r1) / 6, -C_r1 / 6)
-    float ro[9];
-    float fr[8];
+    //   ro[k] = (1 - s_k) / |M_k|^2 for the diagonal rows;
+    //   D2Q9: fr[4 r + j], flux row 3 + 2 r on dl_3, dl_4, dl_5, dl_6
+    //         ((delta_r0 - A_r0) / 6, -C_r0 / 6, (delta_r1 - A_r1) / 6, -C_r1 / 6);
+    //   D3Q15: fr[6 r + 2 b + j], flux row 3 + 2 r on dl_{3 + 2 b} (j = 0) and
+    //         dl_{4 + 2 b} (j = 1): (delta_rb - A_rb) / |M_3|^2, -C_rb / |M_3|^2
+    float ro[15];
+    float fr[18];
     // sum_i w_i - 1 with the FP32 weights the 16-bit decode adds back (w0 + 4 wa
     // + 4 wd for D2Q9, w0 + 6 wa + 8 wd for D3Q15): the rest offset g_0 carries
     // -phi eps0 so that decode and store conserve mass in FP32 as they do exactly
     float eps0;
 };
 
-// Fills ro and fr from s, A and C (D2Q9; host side).
-inline void fold_offset_coef(Coef& c)
+// Fills ro and fr from s, A and C (D2Q9 or D3Q15; host side).
+inline void fold_offset_coef(Coef& c, int q = 9)
 {
-    const double n2[9] = {9, 36, 36, 6, 12, 6, 12, 4, 4};
-    for (int k = 0; k < 9; ++k) c.ro[k] = (float)((1.0 - (double)c.s[k]) / n2[k]);
-    for (int r = 0; r < 2; ++r) {
-        c.fr[4 * r + 0] = (float)(((r == 0 ? 1.0 : 0.0) - (double)c.A[2 * r + 0]) / 6.0);
-        c.fr[4 * r + 1] = (float)(-(double)c.C[2 * r + 0] / 6.0);
-        c.fr[4 * r + 2] = (float)(((r == 1 ? 1.0 : 0.0) - (double)c.A[2 * r + 1]) / 6.0);
-        c.fr[4 * r + 3] = (float)(-(double)c.C[2 * r + 1] / 6.0);
+    if (q == 9) {
+        const double n2[9] = {9, 36, 36, 6, 12, 6, 12, 4, 4};
+        for (int k = 0; k < 9; ++k) c.ro[k] = (float)((1.0 - (double)c.s[k]) / n2[k]);
+        for (int r = 0; r < 2; ++r) {
+            c.fr[4 * r + 0] = (float)(((r == 0 ? 1.0 : 0.0) - (double)c.A[2 * r + 0]) / 6.0);
+            c.fr[4 * r + 1] = (float)(-(double)c.C[2 * r + 0] / 6.0);
+            c.fr[4 * r + 2] = (float)(((r == 1 ? 1.0 : 0.0) - (double)c.A[2 * r + 1]) / 6.0);
+            c.fr[4 * r + 3] = (float)(-(double)c.C[2 * r + 1] / 6.0);
+        }
+        return;
     }
+    // D3Q15 row norms |M_k|^2 of Eq. A.2
+    const double n2[15] = {15, 18, 360, 10, 40, 10, 40, 10, 40, 12, 4, 8, 8, 8, 8};
+    for (int k = 0; k < 15; ++k) c.ro[k] = (float)((1.0 - (double)c.s[k]) / n2[k]);
+    for (int r = 0; r < 3; ++r)
+        for (int b = 0; b < 3; ++b) {
+            c.fr[6 * r + 2 * b] = (float)(((r == b ? 1.0 : 0.0) - (double)c.A[3 * r + b]) / n2[3]);
+            c.fr[6 * r + 2 * b + 1] = (float)(-(double)c.C[3 * r + b] / n2[3]);
+        }
 }
 
 // Tensor maps of the TMA-staged D2Q9 step (k_step_tma_d2q9) for one source
@@ -63,19 +76,6 @@ struct TmaMaps {
     CUtensorMap g, gh;    // 16-bit offsets [9][ny][nx]: boxes (256, 1, 9) and (8, 1, 9)
     CUtensorMap p, ph;    // phi [ny][nx]: boxes (256, 1) and (4, 1)
     CUtensorMap u, uh;    // velocity factors [2][ny][nx]: boxes (256, 1, 2) and (4, 1, 2)
-};
-
-// Tensor maps of the TMA-staged D3Q15 step (k_step_tma_d3q15) for one source
-// buffer; 16-bit offsets as the 4-D tensor [15][nz][ny][nx], phi [nz][ny][nx],
-// velocity factors [3][nz][ny][nx].
-struct TmaMaps15 {
-    CUtensorMap gA;   // offsets, box (128, 1, 1, 5): planes 0 .. 4 (e_z = 0)
-    CUtensorMap gB;   // offsets, box (128, 1, 1, 1): plane 5 or 6 (z axis)
-    CUtensorMap gC;   // offsets, box (128, 1, 1, 4): corners 7 .. 10 or 11 .. 14
-    CUtensorMap hA;   // offsets, box (8, 1, 1, 2): halo of planes 1, 2 (x axis)
-    CUtensorMap hC;   // offsets, box (8, 1, 1, 4): halo of four corners
-    CUtensorMap p, ph;   // phi: boxes (128, 1, 1) and (4, 1, 1)
-    CUtensorMap u, uh;   // velocity factors: boxes (128, 1, 1, 3) and (4, 1, 1, 3)
 };
 
 struct StepArgs {
@@ -99,7 +99,7 @@ struct StepArgs {
     int* status;          // device status word (LBM_E_TIMEOUT from a bounded wait) or nullptr
     long long spin_limit; // SM clock cycles a bounded wait may take (0: give up at once)
     const TmaMaps* tma;   // host pointer: tensor maps of src / phi_src / ua, or nullptr
-    const TmaMaps15* tma15;   // the same for the D3Q15 kernel, or nullptr
+    int zwalk;            // D3Q15 z-walk kernel: planes per CTA (0: chosen by the launcher)
 };
 
 // One reverse-time step (lbm_adjoint.cu).
@@ -163,18 +163,19 @@ inline bool tma_ok(const StepArgs& a, int ukind)
            (ukind != U_FIELD || (reinterpret_cast<uintptr_t>(a.ua) & 15) == 0);
 }
 
-// The TMA-staged D3Q15 kernel needs 128-column strips (nx % 128 == 0), int
-// offsets, a 16-byte aligned velocity field and the tensor maps of the source.
-inline bool tma15_ok(const StepArgs& a, int ukind)
+// The D3Q15 z-walk kernel needs 64-column tiles (nx % 64 == 0), ty-row tiles
+// (ny % ty == 0), int offsets and 16-byte aligned offsets, phi and velocity
+// fields (its shared-memory fills are 16-byte copies).
+inline bool zw_ok(const StepArgs& a, int ukind, int ty)
 {
-    return a.tma15 != nullptr && a.nx % 128 == 0 && 18LL * a.ncell < (1LL << 31) &&
+    return a.nx % 64 == 0 && a.ny % ty == 0 && 18LL * a.ncell < (1LL << 31) &&
+           (reinterpret_cast<uintptr_t>(a.phi_src) & 15) == 0 && (reinterpret_cast<uintptr_t>(a.src) & 15) == 0 &&
            (ukind != U_FIELD || (reinterpret_cast<uintptr_t>(a.ua) & 15) == 0);
 }
 
 // Encode the tensor maps for one source buffer (lbm_tma.cu); false if the
 // driver entry point is missing or the layout breaks a tensor-map rule.
 bool encode_tma_maps(const void* g, const float* phi, const float* ua, int nx, int ny, TmaMaps* out);
-bool encode_tma_maps15(const void* g, const float* phi, const float* ua, int nx, int ny, int nz, TmaMaps15* out);
 
 struct LaunchCfg {
     int block;   // threads per block (multiple of 32)

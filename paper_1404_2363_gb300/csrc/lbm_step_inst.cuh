@@ -5,7 +5,7 @@
 #include "lbm_pair.cuh"
 #include "lbm_pair_d3q15.cuh"
 #include "lbm_tma_d2q9.cuh"
-#include "lbm_tma_d3q15.cuh"
+#include "lbm_zwalk_d3q15.cuh"
 
 namespace lbm {
 
@@ -29,9 +29,9 @@ static cudaError_t step_vec(LaunchCfg cfg, const StepArgs& a, cudaStream_t st)
         }
     }
     if constexpr (L::Q == 15 && STORE != ST_F32) {
-        // TMA-staged rows: two rows per iteration and five stages, or four and seven
-        if (cfg.vec == 7 && tma15_ok(a, UK)) return launch_tma_d3q15<STORE, UK, WALLS, 2, 5>(a, st);
-        if (cfg.vec == 8 && tma15_ok(a, UK)) return launch_tma_d3q15<STORE, UK, WALLS, 4, 7>(a, st);
+        // phi, the velocity factors and the offsets staged in shared memory along a walk in z
+        if (cfg.vec == 9 && cfg.block == 256 && zw_ok(a, UK, 8)) return launch_zw_d3q15<STORE, UK, WALLS, 8>(a, st);
+        if (cfg.vec == 9 && cfg.block == 128 && zw_ok(a, UK, 4)) return launch_zw_d3q15<STORE, UK, WALLS, 4>(a, st);
         if (cfg.vec == 5 && pair_ok(a, UK, L::Q)) {
             // node-pair variant (paired FP32 arithmetic, two adjacent nodes per thread)
             const int per = 2 * cfg.block;

@@ -1,4 +1,4 @@
-// Tensor maps for the TMA-staged D2Q9 and D3Q15 steps (host side). The encoder comes from
+// Tensor maps for the TMA-staged D2Q9 step (host side). The encoder comes from
 // the CUDA driver through the runtime's entry-point query, so the library does
 // not link libcuda.
 #include <cudaTypedefs.h>
@@ -49,40 +49,6 @@ bool encode_tma_maps(const void* g, const float* phi, const float* ua, int nx, i
     if (ok && ua)
         ok = encode(fn, &out->u, ua, 3, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nx, ny, 2, 256) &&
              encode(fn, &out->uh, ua, 3, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nx, ny, 2, 4);
-    else if (ok)
-        out->u = out->uh = out->p;   // not read without a velocity field
-    return ok;
-}
-
-// rank-3 or rank-4 map over [d3][nz][ny][nx] elements of `bytes` each, box (bx, 1, 1[, b3])
-static bool encode3d(PFN_cuTensorMapEncodeTiled_v12000 fn, CUtensorMap* m, const void* base, int rank,
-                     CUtensorMapDataType type, int bytes, int nx, int ny, int nz, int d3, int bx, int b3)
-{
-    const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)d3};
-    const cuuint64_t strides[3] = {(cuuint64_t)nx * bytes, (cuuint64_t)nx * ny * bytes,
-                                   (cuuint64_t)nx * ny * nz * bytes};
-    const cuuint32_t box[4] = {(cuuint32_t)bx, 1u, 1u, (cuuint32_t)b3};
-    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
-    return fn(m, type, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-bool encode_tma_maps15(const void* g, const float* phi, const float* ua, int nx, int ny, int nz, TmaMaps15* out)
-{
-    PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
-    if (!fn || nx % 128 != 0 || ny < 1 || nz < 1) return false;
-    const CUtensorMapDataType u16 = CU_TENSOR_MAP_DATA_TYPE_UINT16, f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    bool ok = encode3d(fn, &out->gA, g, 4, u16, 2, nx, ny, nz, 15, 128, 5) &&
-              encode3d(fn, &out->gB, g, 4, u16, 2, nx, ny, nz, 15, 128, 1) &&
-              encode3d(fn, &out->gC, g, 4, u16, 2, nx, ny, nz, 15, 128, 4) &&
-              encode3d(fn, &out->hA, g, 4, u16, 2, nx, ny, nz, 15, 8, 2) &&
-              encode3d(fn, &out->hC, g, 4, u16, 2, nx, ny, nz, 15, 8, 4) &&
-              encode3d(fn, &out->p, phi, 3, f32, 4, nx, ny, nz, 1, 128, 1) &&
-              encode3d(fn, &out->ph, phi, 3, f32, 4, nx, ny, nz, 1, 4, 1);
-    if (ok && ua)
-        ok = encode3d(fn, &out->u, ua, 4, f32, 4, nx, ny, nz, 3, 128, 3) &&
-             encode3d(fn, &out->uh, ua, 4, f32, 4, nx, ny, nz, 3, 4, 3);
     else if (ok)
         out->u = out->uh = out->p;   // not read without a velocity field
     return ok;

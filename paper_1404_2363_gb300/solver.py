@@ -148,6 +148,10 @@ class Solver:
         """Bound (SM clock cycles) on each device wait of the TMA-staged kernel."""
         self._ck(self.L.lbm_cde_set_wait_limit(self.h, int(cycles)), "lbm_cde_set_wait_limit")
 
+    def set_zwalk(self, planes):
+        """Planes per CTA of the D3Q15 z-walk kernel (0: chosen by the launcher)."""
+        self._ck(self.L.lbm_cde_set_zwalk(self.h, int(planes)), "lbm_cde_set_zwalk")
+
     def autotune(self, steps=20):
         b, v = ctypes.c_int32(), ctypes.c_int32()
         self._ck(self.L.lbm_cde_autotune(self.h, int(steps), ctypes.byref(b), ctypes.byref(v)), "lbm_cde_autotune")

@@ -59,14 +59,19 @@ def test_vortex_4096_windows(O, storage, tol, launch, tau):
         assert_parity(got[np.ix_(iy, ix)][c, c], want[c, c], tol, (x0, y0))
 
 
-@pytest.mark.parametrize("storage,tol,launch", [("f32", 1e-5, None), ("f16", 2e-3, (64, 5)),
-                                               ("bf16", 2e-3, (192, 5)), ("bf16", 2e-3, (128, 1)),
-                                               ("f16", 2e-3, (128, 7)), ("bf16", 2e-3, (128, 7)),
-                                               ("f16", 2e-3, (128, 8)), ("bf16", 2e-3, (128, 8))])
+D3_384 = [("f32", 1e-5, None), ("f16", 2e-3, (64, 5)), ("bf16", 2e-3, (192, 5)), ("bf16", 2e-3, (128, 1)),
+          ("f16", 2e-3, (256, 9)), ("bf16", 2e-3, (256, 9)), ("bf16", 2e-3, (128, 9))]
+
+
+def _launch_id(v):
+    return f"{v[0]}x{v[1]}" if isinstance(v, tuple) else "auto"
+
+
+@pytest.mark.parametrize("storage,tol,launch", D3_384, ids=[f"{s}-{_launch_id(l)}" for s, _, l in D3_384])
 def test_d3q15_384_windows(O, storage, tol, launch):
-    """launch (., 5): the D3Q15 node-pair kernel of the 16-bit forms; (128, 7 / 8)
-    the TMA-staged kernel (bench.py times the autotuner's choice among them);
-    (., 1) the one-node kernel."""
+    """launch (., 5): the D3Q15 node-pair kernel of the 16-bit forms; (., 9) the
+    z-walk kernel (bench.py times the autotuner's choice among them); (., 1) the
+    one-node kernel."""
     N, nsteps, half = 384, 8, 14
     wl = W.d3q15_workload(N)
     s = Solver(lattice=15, nx=N, ny=N, nz=N, storage=storage)
@@ -93,17 +98,19 @@ def test_d3q15_384_windows(O, storage, tol, launch):
         assert_parity(got[np.ix_(iz, iy, ix)][c, c, c], want[c, c, c], tol, (x0, y0, z0))
 
 
-@pytest.mark.parametrize("storage,launch", [("f32", None), ("f16", (64, 5)), ("bf16", (64, 5)),
-                                            ("f16", (64, 1)), ("bf16", (64, 1)), ("f16", (128, 7)),
-                                            ("bf16", (128, 8))])
+D3_1000 = [("f32", None), ("f16", (64, 5)), ("bf16", (64, 5)), ("f16", (64, 1)), ("bf16", (64, 1)),
+           ("f16", (256, 9)), ("bf16", (256, 9))]
+
+
+@pytest.mark.parametrize("storage,launch", D3_1000, ids=[f"{s}-{_launch_id(l)}" for s, l in D3_1000])
 def test_d3q15_1000_steps_error_vs_fp64(O, storage, launch):
     """The D3Q15 workload's recipe (random rotated anisotropic D, divergence-free
-    random u, Gaussian hill) on a 48^3 grid (128 x 48 x 48 for the TMA-staged
-    kernel's 128-column strips) for 1000 steps: relative L2 error of phi against
+    random u, Gaussian hill) on a 48^3 grid (64 x 48 x 48 for the z-walk
+    kernel's 64-column tiles) for 1000 steps: relative L2 error of phi against
     FP64 and the change of the total (conserved exactly by the scheme) stay within
     the bounds of the D2Q9 5000-step test."""
     n, steps = 48, 1000
-    nx = 128 if launch and launch[1] in (7, 8) else n
+    nx = 64 if launch and launch[1] == 9 else n
     wl = W.d3q15_workload(n, shape=(nx, n, n))
     u = wl["u"].astype(np.float32)
     p0 = wl["phi0"].astype(np.float32)

@@ -105,11 +105,13 @@ def test_kernels_without_background(O, storage, bc, ukind, launch):
         assert np.abs(got[walls] - want[walls]).max() <= TOL[storage] * np.abs(want).max()
 
 
-@pytest.mark.parametrize("storage,launch", [("f32", None), ("bf16", (64, 5)), ("f16", (64, 5))])
+@pytest.mark.parametrize("storage,launch", [("f32", None), ("bf16", (64, 5)), ("f16", (64, 5)),
+                                            ("bf16", (256, 9)), ("f16", (256, 9))])
 def test_d3q15_without_background(O, storage, launch):
-    """D3Q15 hill alone (one-node FP32 kernel, node-pair 16-bit kernel), Neumann
-    walls on the y faces; relative L2 and per-element bounds."""
-    case = Case(lattice=15, storage=storage, nx=40, ny=23, nz=17, steps=60, bc=("noflux", "noflux"),
+    """D3Q15 hill alone (one-node FP32 kernel, node-pair and z-walk 16-bit
+    kernels), Neumann walls on the y faces; relative L2 and per-element bounds."""
+    nx, ny = (64, 24) if launch and launch[1] == 9 else (40, 23)
+    case = Case(lattice=15, storage=storage, nx=nx, ny=ny, nz=17, steps=60, bc=("noflux", "noflux"),
                 D=np.diag([0.02, 0.03, 0.04]), bg=False)
     phi0, a, sched = case.inputs()
     if launch is None:
@@ -359,21 +361,41 @@ def test_pair_offset_kernel_d3q15_narrow_grids(O, nx, ny, nz):
         assert_parity(got, want, TOL[storage], (storage, nx, ny, nz))
 
 
-@pytest.mark.parametrize("vec", [7, 8])
+def _run_zw(case, phi0, a, sched, planes, block=256):
+    import torch
+    from paper_1404_2363_gb300.solver import Solver
+
+    s = Solver(lattice=15, nx=case.nx, ny=case.ny, nz=case.nz, storage=case.storage, bc=case.bc,
+               phi_w=case.phi_w, model=case.model)
+    s.set_launch(block, 9)
+    s.set_zwalk(planes)
+    s.set_D(case.D)
+    if a is not None:
+        s.set_velocity(torch.from_numpy(a).cuda(), None if sched is None else torch.from_numpy(sched).cuda(),
+                       kind="row" if case.ukind == "row" else "field")
+    s.set_phi(torch.from_numpy(phi0).cuda())
+    s.step(case.steps)
+    got = s.get_phi().cpu().numpy().astype(np.float64)
+    s.sync()
+    return got
+
+
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 @pytest.mark.parametrize("bc,ukind", [(("periodic", "periodic"), "field"), (("noflux", "noflux"), "row"),
                                       (("bounceback", "bounceback"), "field"),
                                       (("dirichlet", "dirichlet"), "field"), (("periodic", "periodic"), "none")])
-def test_tma_offset_kernel_d3q15(O, storage, bc, ukind, vec):
-    """The TMA-staged D3Q15 kernel of the 16-bit forms (launch vec 7 / 8: a stage
-    holds one grid row at the three planes z - 1, z, z + 1; two or four rows per
-    iteration) against the oracle on a 256 x 13 x 9 grid (two strips, 13 rows: ragged
-    row ranges), and against the node-pair kernel, whose arithmetic it shares."""
-    case = Case(lattice=15, storage=storage, bc=bc, ukind=ukind, sched=ukind != "none", nx=256, ny=13, nz=9,
+@pytest.mark.parametrize("block", [256, 128])
+def test_zwalk_offset_kernel_d3q15(O, storage, bc, ukind, block):
+    """The D3Q15 z-walk kernel of the 16-bit forms (launch vec 9: 64 x 8 or 64 x 4
+    tiles of the (x, y) plane walking z, phi and the velocity factors of three
+    planes and the offsets of a step in shared memory) against the oracle on a
+    128 x 16 x 10 grid: two tiles in x, two or four in y, z ranges of 3, 3 and 4
+    planes (walks of 4 planes per CTA asked), and against the node-pair kernel,
+    whose arithmetic it shares."""
+    case = Case(lattice=15, storage=storage, bc=bc, ukind=ukind, sched=ukind != "none", nx=128, ny=16, nz=10,
                 steps=30, D=D3, phi_w=(1.0, 0.25) if bc[0] == "dirichlet" else (0.0, 0.0))
     phi0, a, sched = case.inputs()
-    got, s = _run_vec3(case, phi0, a, sched, vec=vec, block=128)
-    s.sync()
+    got = _run_zw(case, phi0, a, sched, planes=4, block=block)
     want = run_oracle(O, case, phi0, a, sched)
     assert_parity(got, want, TOL[storage])
     pair, _ = _run_vec3(case, phi0, a, sched, vec=5, block=64)
@@ -382,48 +404,38 @@ def test_tma_offset_kernel_d3q15(O, storage, bc, ukind, vec):
         assert np.abs(got[:, 0] - 1.0).max() < 1e-4 and np.abs(got[:, -1] - 0.25).max() < 1e-4
 
 
-@pytest.mark.parametrize("nx,ny,nz,steps", [(128, 1, 3, 20), (128, 3, 1, 20), (384, 40, 5, 12), (128, 7, 2, 25)])
-def test_tma_d3q15_work_ranges(O, nx, ny, nz, steps):
-    """One strip and one-row / three-row periodic y (every staged row wraps), one
-    and two z planes (the three staged planes coincide or repeat), three strips of
-    40 rows."""
-    for storage, vec in (("f16", 7), ("bf16", 7), ("bf16", 8)):
+@pytest.mark.parametrize("nx,ny,nz,planes,steps", [(64, 8, 1, 0, 20), (64, 8, 2, 2, 20), (64, 8, 2, 1, 20),
+                                                   (128, 24, 5, 0, 16), (192, 16, 7, 7, 16), (64, 40, 9, 2, 12)])
+def test_zwalk_d3q15_work_ranges(O, nx, ny, nz, planes, steps):
+    """One tile with one z plane (the three staged planes coincide, every staged
+    row and column wraps), two planes walked by one CTA or by two, the launcher's
+    own ranges, one walk over all seven planes (its first and last staged planes
+    wrap), and five tiles in y with ranges of one and two planes; 8-row and
+    4-row tiles."""
+    for storage, block in (("f16", 256), ("bf16", 256), ("bf16", 128)):
         case = Case(lattice=15, storage=storage, nx=nx, ny=ny, nz=nz, steps=steps, D=D3)
         phi0, a, sched = case.inputs()
-        got, s = _run_vec3(case, phi0, a, sched, vec=vec, block=128)
-        s.sync()
+        got = _run_zw(case, phi0, a, sched, planes, block)
         want = run_oracle(O, case, phi0, a, sched)
-        assert_parity(got, want, TOL[storage], (storage, vec, nx, ny, nz))
+        assert_parity(got, want, TOL[storage], (storage, block, nx, ny, nz, planes))
 
 
-def test_tma_d3q15_wait_timeout_is_reported_and_handle_recovers(O):
-    """A zero wait limit makes every bounded wait of the TMA-staged D3Q15 kernel
-    give up: LBM_E_TIMEOUT on the next synchronising call, no kernel hangs, and
-    the handle then runs correctly with the default limit."""
-    import torch
+def test_zwalk_rejects_unsupported_shapes():
     from paper_1404_2363_gb300 import _native as N
     from paper_1404_2363_gb300.solver import Solver
 
-    case = Case(lattice=15, storage="bf16", nx=128, ny=16, nz=6, steps=12, D=D3)
-    phi0, a, sched = case.inputs()
-    s = Solver(lattice=15, nx=case.nx, ny=case.ny, nz=case.nz, storage="bf16")
-    s.set_launch(128, 7)
-    s.set_D(case.D)
-    s.set_velocity(torch.from_numpy(a).cuda(), torch.from_numpy(sched).cuda())
-    s.set_phi(torch.from_numpy(phi0).cuda())
-    s.set_wait_limit(0)
-    s.step(3)
-    with pytest.raises(N.LbmError) as e:
-        s.sync()
-    assert e.value.status == N.LBM_E_TIMEOUT
-    s.sync()
-    s.set_wait_limit(4_000_000_000)
-    s.set_phi(torch.from_numpy(phi0).cuda())
-    s.step(case.steps)
-    got = s.get_phi().cpu().numpy().astype(np.float64)
-    s.sync()
-    want = run_oracle(O, case, phi0, a, sched)
-    assert_parity(got, want, TOL["bf16"])
+    for nx, ny, storage, block in ((96, 8, "bf16", 256), (64, 12, "bf16", 256), (64, 8, "f32", 256),
+                                   (64, 6, "f16", 128)):
+        s = Solver(lattice=15, nx=nx, ny=ny, nz=3, storage=storage)
+        with pytest.raises(N.LbmError) as e:
+            s.set_launch(block, 9)
+        assert e.value.status == N.LBM_E_ARG
+    s = Solver(lattice=15, nx=64, ny=8, nz=3, storage="bf16")
+    with pytest.raises(N.LbmError):
+        s.set_launch(64, 9)
+    with pytest.raises(N.LbmError):
+        s.set_zwalk(-1)
+
 
 
 def _run_vec3(case, phi0, a, sched, vec=1, block=256):
