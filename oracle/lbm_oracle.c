@@ -678,8 +678,9 @@ static void collision_matrix(const orc_lattice* L, const orc_params* p, const do
  *   dS       : += dL/dS_kl summed over cells [q*q] (or NULL)
  *   du       : += dL/du_a(x, t)             [dim*ncell] (or NULL)
  * The streaming part is the literal transpose of the push + wall rules in
- * orc_step, applied in reverse order; the collision part multiplies by C^T.
- * Dirichlet walls are affine, not linear, and are rejected here. */
+ * orc_step (walls on any face), applied in reverse order; the collision part
+ * multiplies by C^T. Dirichlet walls are affine, not linear, and are rejected
+ * here. */
 int orc_adjoint_step(const orc_params* p, const double* lam_next, const double* f_pre,
                      const double* u, double* lam_out, double* dS, double* du)
 {
@@ -687,59 +688,62 @@ int orc_adjoint_step(const orc_params* p, const double* lam_next, const double* 
     int rc = build_lattice(&L, p);
     if (rc) return rc;
     if (p->bc_lo == ORC_DIRICHLET || p->bc_hi == ORC_DIRICHLET) return -4;
-    if (p->bcx_lo != ORC_PERIODIC || p->bcz_lo != ORC_PERIODIC) return -4;  /* y-face walls only */
     const int64_t nx = p->nx, ny = p->ny, nz = p->nz, nc = ncells(p);
     const int q = L.q;
-    const int periodic_y = (p->bc_lo == ORC_PERIODIC);
     double* lam = (double*)malloc(sizeof(double) * q * nc);  /* adjoint of f(t+1) before wall fill */
     double* lpost = (double*)calloc((size_t)q * nc, sizeof(double)); /* adjoint of f'(t) */
     if (!lam || !lpost) { free(lam); free(lpost); return -10; }
     memcpy(lam, lam_next, sizeof(double) * q * nc);
     int opp[ORC_MAXQ];
     for (int i = 0; i < q; ++i) opp[i] = opposite(&L, i);
-    /* transpose of wall_fill (NOFLUX_NODE: f_i = f_mirror(i) at the wall node) */
-    if (!periodic_y) {
-        for (int side = 0; side < 2; ++side) {
-            const int kind = side == 0 ? p->bc_lo : p->bc_hi;
-            if (kind != ORC_NOFLUX_NODE) continue;
-            const int64_t y = side == 0 ? 0 : ny - 1;
-            const int inward = side == 0 ? +1 : -1;
-            for (int64_t z = 0; z < nz; ++z)
+    if (any_wall(p)) {
+        /* transpose of the NOFLUX_NODE fill of wall_fill: at a wall node the
+         * populations whose source lies beyond NOFLUX_NODE faces took the value
+         * (before the fill) of the population reflected in those axes */
+        for (int64_t z = 0; z < nz; ++z)
+            for (int64_t y = 0; y < ny; ++y)
                 for (int64_t x = 0; x < nx; ++x) {
+                    if (!on_wall(p, x, y, z)) continue;
                     const int64_t c = x + nx * (y + ny * z);
-                    for (int i = 0; i < q; ++i)
-                        if (L.e[i][1] == inward) {
-                            lam[mirror_y(&L, i) * nc + c] += lam[i * nc + c];
-                            lam[i * nc + c] = 0.0;
-                        }
+                    double acc[ORC_MAXQ] = {0.0};
+                    for (int i = 0; i < q; ++i) {
+                        int bb, nf;
+                        beyond(&L, p, i, x, y, z, &bb, &nf);
+                        acc[nf ? reflect(&L, i, nf) : i] += lam[i * nc + c];
+                    }
+                    for (int i = 0; i < q; ++i) lam[i * nc + c] = acc[i];
                 }
-        }
-        /* transpose of bounce-back: f_opp(i)(x) = f'_i(x) */
-        for (int side = 0; side < 2; ++side) {
-            const int kind = side == 0 ? p->bc_lo : p->bc_hi;
-            if (kind != ORC_BOUNCEBACK) continue;
-            const int64_t y = side == 0 ? 0 : ny - 1;
-            const int outward = side == 0 ? -1 : +1;
-            for (int64_t z = 0; z < nz; ++z)
+        /* transpose of bounce-back: f_opp(i)(x) = f'_i(x) where the source of
+         * opp(i) lies beyond a BOUNCEBACK face */
+        for (int64_t z = 0; z < nz; ++z)
+            for (int64_t y = 0; y < ny; ++y)
                 for (int64_t x = 0; x < nx; ++x) {
+                    if (!on_wall(p, x, y, z)) continue;
                     const int64_t c = x + nx * (y + ny * z);
-                    for (int i = 0; i < q; ++i)
-                        if (L.e[i][1] == outward) lpost[i * nc + c] += lam[opp[i] * nc + c];
+                    for (int i = 0; i < q; ++i) {
+                        int bb, nf;
+                        if (beyond(&L, p, opp[i], x, y, z, &bb, &nf) && bb) lpost[i * nc + c] += lam[opp[i] * nc + c];
+                    }
                 }
-        }
     }
-    /* transpose of the push (Eq. 5) */
+    /* transpose of the push (Eq. 5): populations that leave through a wall carry nothing */
+    const int per[3] = {p->bcx_lo == ORC_PERIODIC, p->bc_lo == ORC_PERIODIC, p->bcz_lo == ORC_PERIODIC};
+    const int64_t n[3] = {nx, ny, nz};
     for (int i = 0; i < q; ++i)
         for (int64_t z = 0; z < nz; ++z)
             for (int64_t y = 0; y < ny; ++y)
                 for (int64_t x = 0; x < nx; ++x) {
                     const int64_t c = x + nx * (y + ny * z);
-                    int64_t yd = y + L.e[i][1];
-                    if (periodic_y) yd = wrap(yd, ny);
-                    else if (yd < 0 || yd >= ny) continue;
-                    const int64_t xd = wrap(x + L.e[i][0], nx);
-                    const int64_t zd = wrap(z + L.e[i][2], nz);
-                    lpost[i * nc + c] += lam[i * nc + xd + nx * (yd + ny * zd)];
+                    const int64_t r[3] = {x, y, z};
+                    int64_t d[3];
+                    int out = 0;
+                    for (int a = 0; a < 3; ++a) {
+                        d[a] = r[a] + L.e[i][a];
+                        if (per[a]) d[a] = wrap(d[a], n[a]);
+                        else if (d[a] < 0 || d[a] >= n[a]) out = 1;
+                    }
+                    if (out) continue;
+                    lpost[i * nc + c] += lam[i * nc + d[0] + nx * (d[1] + ny * d[2])];
                 }
     /* transpose of the collision: lam(t) = C^T lam'(t) ; parameter and velocity partials */
     set_threads(p);

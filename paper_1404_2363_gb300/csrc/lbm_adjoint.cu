@@ -69,9 +69,19 @@ int adjoint_rows(long long nx, long long ny, long long nz, int sms)
 // instructions), long long otherwise. The maps M f, M mu and M^T c use the
 // same sums and differences of same-speed populations as the forward step
 // (moments / populations): the kernel is bound by its instruction issue.
-template <class L, int UK, bool WALLS, bool DA, typename IX>
-__global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(const AdjArgs a)
+// WM: 0 periodic; 1 walls on the y faces (the rules in place below); 2 walls
+// on any face (BOX): each pull source found as in k_step_box, and the push
+// scatters nu_i to the address the forward pull of population i read: the
+// regular source (j, x - e_j), or for a bounce-back face the node's own
+// reversed population (opp j, x), j being i or, where the source lies beyond
+// NOFLUX_NODE faces, i reflected in those axes. Each address is read by the
+// pulls of one node only, so every thread writes its own addresses: (j, x - e_j)
+// for the sources in range, and (k, x) for the populations that leave through
+// a wall (zero unless a bounce-back pull read them).
+template <class L, int UK, int WM, bool DA, typename IX>
+__global__ void __launch_bounds__(256, (L::Q == 9 && !DA && WM < 2) ? 4 : 3) k_adjoint(const AdjArgs a)
 {
+    constexpr bool WALLS = WM == 1, BOX = WM == 2;
     constexpr int Q = L::Q, DIM = L::DIM, NG = ngrad<L>();
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -109,10 +119,59 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(con
 #pragma unroll
             for (int d = 0; d < DIM; ++d) du_old[d] = a.du_acc[(IX)d * N + cell];
         }
+        // BOX: pull source of every population (in range after periodic wrap, or
+        // beyond a wall: bounce-back flag, mask of the NOFLUX_NODE axes)
+        IX bsrc[Q];
+        bool bout[Q], bbb[Q];
+        int bnf[Q];
+        if constexpr (BOX) {
+            const int pos[3] = {xc, y, z}, n3[3] = {nx, ny, nz};
+            const int klo[3] = {a.bcx_lo, a.bc_lo, a.bcz_lo}, khi[3] = {a.bcx_hi, a.bc_hi, a.bcz_hi};
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int e[3] = {L::ex(i), L::ey(i), L::ez(i)};
+                int sp[3];
+                bout[i] = false;
+                bbb[i] = false;
+                bnf[i] = 0;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    sp[d] = pos[d] - e[d];
+                    if (e[d] == 0) continue;
+                    if (klo[d] == BC_PERIODIC) {
+                        sp[d] = sp[d] < 0 ? sp[d] + n3[d] : (sp[d] >= n3[d] ? sp[d] - n3[d] : sp[d]);
+                    } else if (sp[d] < 0 || sp[d] >= n3[d]) {
+                        const int kind = sp[d] < 0 ? klo[d] : khi[d];
+                        bout[i] = true;
+                        bbb[i] = bbb[i] || kind == BC_BOUNCE;
+                        if (kind == BC_NOFLUX) bnf[i] |= 1 << d;
+                    }
+                }
+                bsrc[i] = bout[i] ? cell : (IX)sp[0] + (IX)nx * ((IX)sp[1] + (IX)ny * (IX)sp[2]);
+            }
+        }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             mu[i] = __ldg(a.mu_in + (IX)i * N + cell);
-            f[i] = __ldg(a.fprev + (IX)i * N + tgt(i));
+            if constexpr (BOX) {
+                f[i] = !bout[i] ? __ldg(a.fprev + (IX)i * N + bsrc[i])
+                                : (bbb[i] ? __ldg(a.fprev + (IX)opposite<L>(i) * N + cell) : 0.f);
+            } else {
+                f[i] = __ldg(a.fprev + (IX)i * N + tgt(i));
+            }
+        }
+        if constexpr (BOX) {
+            float w[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) w[i] = f[i];
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if (bnf[i]) {
+                    const int j = reflect_mask<L>(i, bnf[i]);
+#pragma unroll
+                    for (int k = 0; k < Q; ++k)
+                        if (k == j) f[i] = w[k];
+                }
         }
         const bool lo = WALLS && y == 0 && a.bc_lo != BC_PERIODIC;
         const bool hi = WALLS && y == ny - 1 && a.bc_hi != BC_PERIODIC;
@@ -215,6 +274,28 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA) ? 4 : 3) k_adjoint(con
 
         // push nu with the transposed wall rules
         float* out = a.mu_out;
+        if constexpr (BOX) {
+            float reg[Q], own[Q];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) reg[k] = own[k] = 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int t = bnf[i] ? reflect_mask<L>(i, bnf[i]) : i;   // population whose value i took
+#pragma unroll
+                for (int k = 0; k < Q; ++k)
+                    if (k == t) {
+                        if (!bout[k]) reg[k] += nu[i];
+                        else if (bbb[k]) own[opposite<L>(k)] += nu[i];
+                    }
+            }
+#pragma unroll
+            for (int j = 0; j < Q; ++j)
+                if (!bout[j]) out[(IX)j * N + bsrc[j]] = reg[j];
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+                if (bout[opposite<L>(k)]) out[(IX)k * N + cell] = own[k];   // k leaves through a wall
+            continue;
+        }
         if (lo || hi) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -359,49 +440,55 @@ static cudaError_t grad_reduce(const AdjArgs& a, float* base, int nslice, long l
     return cudaGetLastError();
 }
 
-template <class L, int UK, typename IX>
-static cudaError_t adj_ix(bool walls, const AdjArgs& a, cudaStream_t st, bool reduce)
+template <class L, int UK, typename IX, int WM>
+static cudaError_t adj_wm(const AdjArgs& a, cudaStream_t st, bool reduce)
 {
     dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)((a.ny + a.rows - 1) / a.rows), (unsigned)a.nz);
     if constexpr (UK == U_FIELD) {
         if (a.du_acc != nullptr) {
-            if (walls) k_adjoint<L, UK, true, true, IX><<<grid, 256, 0, st>>>(a);
-            else k_adjoint<L, UK, false, true, IX><<<grid, 256, 0, st>>>(a);
+            k_adjoint<L, UK, WM, true, IX><<<grid, 256, 0, st>>>(a);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess || !reduce) return e;
             return grad_reduce<L>(a, a.partials, 1, 0, st);
         }
     }
     {
-        if (walls) k_adjoint<L, UK, true, false, IX><<<grid, 256, 0, st>>>(a);
-        else k_adjoint<L, UK, false, false, IX><<<grid, 256, 0, st>>>(a);
+        k_adjoint<L, UK, WM, false, IX><<<grid, 256, 0, st>>>(a);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !reduce) return e;
     return grad_reduce<L>(a, a.partials, 1, 0, st);
 }
 
+template <class L, int UK, typename IX>
+static cudaError_t adj_ix(int wmode, const AdjArgs& a, cudaStream_t st, bool reduce)
+{
+    if (wmode == 2) return adj_wm<L, UK, IX, 2>(a, st, reduce);
+    if (wmode == 1) return adj_wm<L, UK, IX, 1>(a, st, reduce);
+    return adj_wm<L, UK, IX, 0>(a, st, reduce);
+}
+
 template <class L, int UK>
-static cudaError_t adj_w(bool walls, const AdjArgs& a, cudaStream_t st, bool reduce)
+static cudaError_t adj_w(int wmode, const AdjArgs& a, cudaStream_t st, bool reduce)
 {
     // 32-bit offsets when every plane (and the velocity planes) fits
-    if ((long long)(L::Q + L::DIM) * a.ncell < (1LL << 31)) return adj_ix<L, UK, int>(walls, a, st, reduce);
-    return adj_ix<L, UK, long long>(walls, a, st, reduce);
+    if ((long long)(L::Q + L::DIM) * a.ncell < (1LL << 31)) return adj_ix<L, UK, int>(wmode, a, st, reduce);
+    return adj_ix<L, UK, long long>(wmode, a, st, reduce);
 }
 
 template <class L>
-static cudaError_t adj_u(int uk, bool walls, const AdjArgs& a, cudaStream_t st, bool reduce)
+static cudaError_t adj_u(int uk, int wmode, const AdjArgs& a, cudaStream_t st, bool reduce)
 {
     switch (uk) {
-        case U_FIELD: return adj_w<L, U_FIELD>(walls, a, st, reduce);
-        case U_ROW: return adj_w<L, U_ROW>(walls, a, st, reduce);
-        default: return adj_w<L, U_NONE>(walls, a, st, reduce);
+        case U_FIELD: return adj_w<L, U_FIELD>(wmode, a, st, reduce);
+        case U_ROW: return adj_w<L, U_ROW>(wmode, a, st, reduce);
+        default: return adj_w<L, U_NONE>(wmode, a, st, reduce);
     }
 }
 
-cudaError_t launch_adjoint(int q, int ukind, bool walls, const AdjArgs& a, cudaStream_t st, bool reduce)
+cudaError_t launch_adjoint(int q, int ukind, int wmode, const AdjArgs& a, cudaStream_t st, bool reduce)
 {
-    return q == 9 ? adj_u<D2Q9>(ukind, walls, a, st, reduce) : adj_u<D3Q15>(ukind, walls, a, st, reduce);
+    return q == 9 ? adj_u<D2Q9>(ukind, wmode, a, st, reduce) : adj_u<D3Q15>(ukind, wmode, a, st, reduce);
 }
 
 cudaError_t launch_grad_reduce(int q, const AdjArgs& a, float* base, int nslice, long long slice, cudaStream_t st)

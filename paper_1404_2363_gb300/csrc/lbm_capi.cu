@@ -813,10 +813,15 @@ static lbm_status adjoint_supported(lbm_cde_t h)
         return fail(h, LBM_E_UNSUPPORTED, "the adjoint needs FP32 state storage");
     if (h->d.bc_lo_y == LBM_BC_DIRICHLET || h->d.bc_hi_y == LBM_BC_DIRICHLET)
         return fail(h, LBM_E_UNSUPPORTED, "the adjoint does not support Dirichlet walls");
-    if (h->d.bc_lo_x != LBM_BC_PERIODIC || h->d.bc_lo_z != LBM_BC_PERIODIC)
-        return fail(h, LBM_E_UNSUPPORTED, "the adjoint supports walls on the y faces only");
     if (!h->d_set) return fail(h, LBM_E_STATE, "set_D must come first");
     return LBM_OK;
+}
+
+// wall mode of the adjoint kernel: 0 periodic, 1 walls on the y faces only, 2 walls on x or z faces
+static int adjoint_wmode(lbm_cde_t h)
+{
+    if (h->d.bc_lo_x != LBM_BC_PERIODIC || h->d.bc_lo_z != LBM_BC_PERIODIC) return 2;
+    return h->d.bc_lo_y != LBM_BC_PERIODIC ? 1 : 0;
 }
 
 static lbm_status ensure_adjoint_buffers(lbm_cde_t h)
@@ -856,6 +861,10 @@ static lbm::AdjArgs make_adj(lbm_cde_t h, int64_t k, const float* mu_in, float* 
     a.ncell = h->ncell;
     a.bc_lo = h->d.bc_lo_y;
     a.bc_hi = h->d.bc_hi_y;
+    a.bcx_lo = h->d.bc_lo_x;
+    a.bcx_hi = h->d.bc_hi_x;
+    a.bcz_lo = h->d.bc_lo_z;
+    a.bcz_hi = h->d.bc_hi_z;
     a.c = h->coef;
     a.du_acc = du;
     a.partials = h->adj_partials;
@@ -878,7 +887,7 @@ lbm_status lbm_cde_adjoint_step(lbm_cde_t h, int64_t k, const float* mu_k_dev, f
     if (reinterpret_cast<uintptr_t>(grad_acc_dev) % 8 != 0) return fail(h, LBM_E_ARG, "grad_acc_dev not 8-byte aligned");
     lbm::AdjArgs a = make_adj(h, k, mu_k_dev, mu_prev_dev, f_prev_dev, dL_da_dev,
                               reinterpret_cast<float2*>(grad_acc_dev));
-    CK(h, lbm::launch_adjoint(h->q, ukind_internal(h->ukind), h->d.bc_lo_y != LBM_BC_PERIODIC, a, h->st, true));
+    CK(h, lbm::launch_adjoint(h->q, ukind_internal(h->ukind), adjoint_wmode(h), a, h->st, true));
     return LBM_OK;
 }
 
@@ -1094,7 +1103,7 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
             lbm::AdjArgs a = make_adj(h, k, h->mu[cur], h->mu[1 - cur], seg_state(j, k - 1 - start), dL_da_dev,
                                       h->grad_acc);
             a.partials = h->adj_partials + nslice * slice;
-            CK(h, lbm::launch_adjoint(h->q, uk, walls, a, h->st, false));
+            CK(h, lbm::launch_adjoint(h->q, uk, adjoint_wmode(h), a, h->st, false));
             if (++nslice == lbm::ADJ_SLICES) {
                 CK(h, lbm::launch_grad_reduce(h->q, a, h->adj_partials, nslice, slice, h->st));
                 nslice = 0;

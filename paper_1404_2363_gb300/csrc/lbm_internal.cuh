@@ -115,7 +115,9 @@ struct AdjArgs {
     int rows;             // grid rows per block (adjoint_rows)
     int nx, ny, nz;
     long long ncell;
-    int bc_lo, bc_hi;
+    int bc_lo, bc_hi;     // y faces
+    int bcx_lo, bcx_hi;   // x faces (wall mode 2)
+    int bcz_lo, bcz_hi;   // z faces (wall mode 2)
     Coef c;
     float* du_acc;        // dL/da accumulator [dim][ncell] (FIELD velocity) or nullptr
     float* partials;      // per-block gradient partials [ngrad][nblocks] (one slice per step)
@@ -195,7 +197,8 @@ cudaError_t launch_sum(int q, int store, const StepArgs& a, double* partials, in
 // a backward sweep writes the partials of up to ADJ_SLICES consecutive steps to
 // separate slices (AdjArgs::partials = base + slice * adjoint_slice_size) and
 // reduces them together with launch_grad_reduce.
-cudaError_t launch_adjoint(int q, int ukind, bool walls, const AdjArgs& a, cudaStream_t st, bool reduce);
+// wmode: 0 periodic, 1 walls on the y faces only, 2 walls on x or z faces (any face)
+cudaError_t launch_adjoint(int q, int ukind, int wmode, const AdjArgs& a, cudaStream_t st, bool reduce);
 cudaError_t launch_grad_reduce(int q, const AdjArgs& a, float* base, int nslice, long long slice, cudaStream_t st);
 long long adjoint_slice_size(int q, long long nx, long long ny, long long nz, int sms);
 constexpr int ADJ_SLICES = 16;   // reverse steps whose block partials are kept apart before one reduction

@@ -218,6 +218,60 @@ def test_d3q15_adjoint_matches_oracle_and_fd(O):
         assert abs(an - fd) <= 1e-4 * abs(fd) + 1e-7, (i, j, an, fd)
 
 
+BOX_ADJ = [
+    Case(nx=37, ny=29, steps=40, bc=("bounceback", "noflux"), bc_x=("noflux", "bounceback")),
+    Case(nx=40, ny=30, steps=40, bc_x=("bounceback", "bounceback")),
+    Case(nx=33, ny=27, steps=40, bc=("noflux", "noflux"), bc_x=("noflux", "noflux"), ukind="row"),
+    Case(lattice=15, nx=12, ny=10, nz=9, steps=20, bc=("noflux", "noflux"), bc_x=("bounceback", "bounceback"),
+         bc_z=("noflux", "bounceback"),
+         D=np.array([[0.03, 0.004, -0.003], [0.004, 0.025, 0.002], [-0.003, 0.002, 0.035]])),
+]
+
+
+@pytest.mark.parametrize("case", BOX_ADJ, ids=lambda c: f"q{c.lattice}-x{c.bc_x[0]}-{c.bc_x[1]}-y{c.bc[0]}-{c.ukind}")
+def test_adjoint_with_walls_on_x_and_z_faces(O, case):
+    """Walls on the x (and z) faces, meeting the y walls at edges and corners:
+    the reverse-time kernel's wall mode 2 (each pull source found as in the
+    forward box kernel, the push scattering to the address the pull read)
+    against the FP64 oracle adjoint, whose walls on any face are pinned as the
+    transpose of the assembled step (tests/test_oracle_adjoint.py)."""
+    phi0, a, sched = case.inputs()
+    g = np.random.default_rng(8).standard_normal(case.shape)
+    s = Solver(lattice=case.lattice, nx=case.nx, ny=case.ny, nz=case.nz, bc=case.bc, bc_x=case.bc_x,
+               bc_z=case.bc_z or ("periodic", "periodic"))
+    s.set_D(case.D)
+    if a is not None:
+        s.set_velocity(torch.from_numpy(a).cuda(), None if sched is None else torch.from_numpy(sched).cuda(),
+                       kind="row" if case.ukind == "row" else "field")
+    s.forward_ckpt(torch.from_numpy(phi0).cuda(), case.steps)
+    want_da = case.ukind == "field"
+    dphi0, dD, _, da = s.backward(torch.from_numpy(g.astype(np.float32)).cuda(), want_da=want_da)
+    s.close()
+    wp, wD, wa = oracle_grads(O, case, phi0, a, sched, g)
+    assert rel_l2(dphi0.cpu().numpy().astype(np.float64), wp) < 1e-5
+    if want_da:
+        assert rel_l2(da.cpu().numpy().astype(np.float64), wa) < 1e-4
+    if wD is not None:
+        assert np.abs(dD - wD).max() <= 1e-4 * np.abs(wD).max()
+    else:   # D3Q15: dL/dD against FP64 central differences of the oracle
+        uf = case.u_of_t(a, sched)
+        h = 1e-6
+        for (i, j) in ((0, 0), (1, 2)):
+            vals = []
+            for sgn in (1, -1):
+                Dp = case.D.copy()
+                Dp[i, j] += sgn * h
+                if i != j:
+                    Dp[j, i] += sgn * h
+                p = oracle_params(O, Case(lattice=15, nx=case.nx, ny=case.ny, nz=case.nz, D=Dp, bc=case.bc,
+                                          bc_x=case.bc_x, bc_z=case.bc_z))
+                phi = O.run(p, phi0.astype(np.float64).reshape(-1), case.steps, u_of_t=uf)
+                vals.append(float((g.reshape(-1) * phi).sum()))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = dD[i, j] + (dD[j, i] if i != j else 0.0)
+            assert abs(an - fd) <= 1e-4 * abs(fd) + 1e-7, (i, j, an, fd)
+
+
 def test_single_step_api_matches_backward():
     """lbm_cde_adjoint_step driven step by step from the host (forward states kept
     with get_state, compensated FP32 gradient accumulators) gives the same dL/dD

@@ -159,19 +159,6 @@ def test_walls_on_x_and_z_faces(O, lattice, storage, bcx, bcy, bcz):
     s.close()
 
 
-def test_box_walls_reject_the_adjoint():
-    import torch
-    from paper_1404_2363_gb300 import _native as N
-    from paper_1404_2363_gb300.solver import Solver
-
-    s = Solver(nx=16, ny=12, bc_x=("noflux", "noflux"))
-    s.set_D(np.diag([0.02, 0.03]))
-    with pytest.raises(N.LbmError) as e:
-        s.forward_ckpt(torch.ones((12, 16), device="cuda"), 4)
-    assert e.value.status == N.LBM_E_UNSUPPORTED
-    s.close()
-
-
 @pytest.mark.parametrize("vec,block", [(1, 64), (2, 128)])
 def test_launch_shapes_agree(vec, block):
     """The same step under other launch shapes gives the identical result."""
