@@ -74,6 +74,7 @@ struct CellArgs {
     long long ncat;
     int ninst;            // instances of this launch
     int tile_base;        // first cell tile of this launch
+    int koff;             // this launch computes step *kdev + 1 + koff
     InstK inst[CELL_INST];
 };
 
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(256) k_batch_cells(const __grid_constant__ Cel
         else hi = mid - 1;
     }
     const InstK& I = a.inst[lo];
-    cell_tile<IX>(I, t - I.tile0, *a.kdev + 1, a.buf, a.ncat, a.strip + (long long)(a.tile_base + t) * 32);
+    cell_tile<IX>(I, t - I.tile0, *a.kdev + 1 + a.koff, a.buf, a.ncat, a.strip + (long long)(a.tile_base + t) * 32);
 }
 
 // Eq. 47 moments of step k for PER_STEP mode, two deterministic passes.
@@ -419,9 +420,9 @@ __device__ __forceinline__ void col_moments(const BatchArgs& a, long long k, int
 
 __global__ void __launch_bounds__(256) k_batch_col_moments(const BatchArgs a, const float* __restrict__ strip,
                                                            const int* __restrict__ cblk_inst,
-                                                           double* __restrict__ cpart)
+                                                           double* __restrict__ cpart, int koff)
 {
-    col_moments(a, *a.kdev + 1, blockIdx.x, strip, cblk_inst, cpart);
+    col_moments(a, *a.kdev + 1 + koff, blockIdx.x, strip, cblk_inst, cpart);
 }
 
 // Pass 2 for instance i (one warp): block partials added in index order with a
@@ -450,11 +451,12 @@ __device__ __forceinline__ void inst_moments(const BatchArgs& a, long long k, in
     }
 }
 
-__global__ void __launch_bounds__(256) k_batch_inst_moments(const BatchArgs a, const double* __restrict__ cpart)
+__global__ void __launch_bounds__(256) k_batch_inst_moments(const BatchArgs a, const double* __restrict__ cpart,
+                                                            int koff)
 {
     const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
     if (i >= a.ninst) return;
-    inst_moments(a, *a.kdev + 1, i, cpart);
+    inst_moments(a, *a.kdev + 1 + koff, i, cpart);
 }
 
 // PERSISTENT mode on cell tiles (tile height 0): one cooperative launch runs
@@ -545,11 +547,21 @@ static int occupancy_grid(const void* fn)
     return std::max(1, per) * sms;
 }
 
+// Streams and events of the PER_STEP launches: the moment passes of step k run
+// on st2 while the cells of step k + 1 run on the batch's stream.
+struct StepStreams {
+    cudaStream_t st2;
+    cudaEvent_t cells_done;       // recorded after the cell launches of a step
+    cudaEvent_t moments_done[2];  // after the moment passes of a step, by step parity
+    float* strip2;                // the column sums of the odd steps
+};
+
 // rows > 0: PERSISTENT on warp tiles of that height; rows == 0: on cell tiles
 static cudaError_t launch_mode(int mode, int rows, const BatchArgs& a, const InstK* cinst, const int* tile_inst,
                                int ninst, long long* kdev,
                                const std::vector<CellArgs>& cells, const std::vector<int>& cell_tiles, int nctiles,
-                               float* strip, const int* cblk_inst, int ncblk, double* cpart, cudaStream_t st)
+                               float* strip, const int* cblk_inst, int ncblk, double* cpart, cudaStream_t st,
+                               const StepStreams& ss)
 {
     // 32-bit offsets when the last plane offset 9 ncat fits in 31 bits
     const bool i32 = 9LL * a.ncat < (1LL << 31);
@@ -582,15 +594,35 @@ static cudaError_t launch_mode(int mode, int rows, const BatchArgs& a, const Ins
         k_batch_advance<<<1, 1, 0, st>>>(kdev, a.nsteps);
         return cudaGetLastError();
     }
-    for (int s = 0; s < a.nsteps; ++s) {
-        for (size_t g = 0; g < cells.size(); ++g) {
-            if (i32) k_batch_cells<int><<<(unsigned)cell_tiles[g], 256, 0, st>>>(cells[g]);
-            else k_batch_cells<long long><<<(unsigned)cell_tiles[g], 256, 0, st>>>(cells[g]);
+    // PER_STEP: step s reads the step index *kdev + 1 + s (one advance at the end),
+    // writes its column sums to the strip buffer of its parity, and leaves its two
+    // moment passes to st2, so that they overlap the cells of step s + 1; the
+    // cells of step s + 2 wait for the moment passes of step s (the strip buffer).
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < a.nsteps && e == cudaSuccess; ++s) {
+        float* sb = (s & 1) ? ss.strip2 : strip;
+        if (s >= 2) e = cudaStreamWaitEvent(st, ss.moments_done[s & 1], 0);
+        for (size_t g = 0; g < cells.size() && e == cudaSuccess; ++g) {
+            CellArgs ca = cells[g];
+            ca.strip = sb;
+            ca.koff = s;
+            if (i32) k_batch_cells<int><<<(unsigned)cell_tiles[g], 256, 0, st>>>(ca);
+            else k_batch_cells<long long><<<(unsigned)cell_tiles[g], 256, 0, st>>>(ca);
+            e = cudaGetLastError();
         }
-        k_batch_col_moments<<<(unsigned)ncblk, 256, 0, st>>>(a, strip, cblk_inst, cpart);
-        k_batch_inst_moments<<<(unsigned)((a.ninst + 7) / 8), 256, 0, st>>>(a, cpart);
-        k_batch_advance<<<1, 1, 0, st>>>(kdev, 1);
+        if (e == cudaSuccess) e = cudaEventRecord(ss.cells_done, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ss.st2, ss.cells_done, 0);
+        if (e != cudaSuccess) break;
+        k_batch_col_moments<<<(unsigned)ncblk, 256, 0, ss.st2>>>(a, sb, cblk_inst, cpart, s);
+        k_batch_inst_moments<<<(unsigned)((a.ninst + 7) / 8), 256, 0, ss.st2>>>(a, cpart, s);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(ss.moments_done[s & 1], ss.st2);
     }
+    if (e != cudaSuccess) return e;
+    // the last moment passes (and with them every earlier one) before the advance
+    if (a.nsteps > 0) e = cudaStreamWaitEvent(st, ss.moments_done[(a.nsteps - 1) & 1], 0);
+    if (e != cudaSuccess) return e;
+    k_batch_advance<<<1, 1, 0, st>>>(kdev, a.nsteps);
     return cudaGetLastError();
 }
 
@@ -627,7 +659,8 @@ struct lbm_cde_batch_s {
     int* tile_inst = nullptr;           // instance of every cell tile (cell-tile PERSISTENT mode)
     int nctiles = 0;                    // cell tiles in all
     std::vector<int> cell_tiles;        // cell tiles of each launch
-    float* strip = nullptr;             // [cell tiles][32] column sums
+    float* strip = nullptr;             // [cell tiles][32] column sums (even steps in PER_STEP mode)
+    lbm::StepStreams ss{};              // PER_STEP: moment stream, events, odd-step column sums
     int* cblk_inst = nullptr;           // instance of each 256-column block of the moment pass
     int ncblk = 0;
     double* cpart = nullptr;            // [ncblk][3] moment partials
@@ -731,7 +764,7 @@ static cudaError_t launch_batch(lbm_cde_batch_t b, const lbm::BatchArgs& a)
 {
     return lbm::launch_mode(b->mode, b->rows, a, b->cinst.data(), b->tile_inst, b->n, b->kdev, b->cells, b->cell_tiles,
                             b->nctiles,
-                            b->strip, b->cblk_inst, b->ncblk, b->cpart, b->st);
+                            b->strip, b->cblk_inst, b->ncblk, b->cpart, b->st, b->ss);
 }
 
 static void drop_graph(lbm_cde_batch_t b)
@@ -903,10 +936,20 @@ lbm_status lbm_cde_batch_create(const lbm_cde_channel_desc* descs, int32_t n, co
     b->kdev = reinterpret_cast<long long*>(b->sync + 6);
     b->moments = static_cast<double*>(balloc(b, sizeof(double) * 3 * (size_t)n * b->chunk));
     b->strip = static_cast<float*>(balloc(b, sizeof(float) * 32 * (size_t)ncell_tiles));
+    b->ss.strip2 = static_cast<float*>(balloc(b, sizeof(float) * 32 * (size_t)ncell_tiles));
+    if (cudaStreamCreateWithFlags(&b->ss.st2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ss.cells_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ss.moments_done[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ss.moments_done[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        lbm_cde_batch_destroy(b);
+        return bfail(nullptr, LBM_E_CUDA, "batch stream or event creation failed");
+    }
     b->ncblk = (int)(b->inst[n - 1].cblk0 + b->inst[n - 1].ncblk);
     b->cblk_inst = static_cast<int*>(balloc(b, sizeof(int) * (size_t)b->ncblk));
     b->cpart = static_cast<double*>(balloc(b, sizeof(double) * 3 * (size_t)b->ncblk));
-    if (!b->inst_dev || !b->buf[0] || !b->buf[1] || !b->sync || !b->moments || !b->strip || !b->cblk_inst ||
+    if (!b->inst_dev || !b->buf[0] || !b->buf[1] || !b->sync || !b->moments || !b->strip || !b->ss.strip2 ||
+        !b->cblk_inst ||
         !b->cpart) {
         lbm_cde_batch_destroy(b);
         return bfail(nullptr, LBM_E_OOM, "batch allocation failed");
@@ -999,6 +1042,14 @@ lbm_status lbm_cde_batch_destroy(lbm_cde_batch_t b)
     bfree(b, b->sync);
     bfree(b, b->moments);
     bfree(b, b->strip);
+    bfree(b, b->ss.strip2);
+    if (b->ss.st2) {
+        cudaStreamSynchronize(b->ss.st2);
+        cudaStreamDestroy(b->ss.st2);
+    }
+    if (b->ss.cells_done) cudaEventDestroy(b->ss.cells_done);
+    for (int p = 0; p < 2; ++p)
+        if (b->ss.moments_done[p]) cudaEventDestroy(b->ss.moments_done[p]);
     bfree(b, b->cblk_inst);
     bfree(b, b->cpart);
     bfree(b, b->tile_inst);
