@@ -143,6 +143,10 @@ __global__ void __launch_bounds__(TmaShape<TMA_R, TMA_NS>::threads)
     float s_now[3], s_prev[3];
     sched_row_at(a.sched, a.srow_now, 2, s_now);
     sched_row_at(a.sched, a.srow_prev, 2, s_prev);
+    // decode slopes k_i s_d(k - 1) of the axis (a) and diagonal (d) populations: the
+    // schedule factor folded in, so a diagonal population costs two paired FMAs
+    const float kax = __fmul_rn(c.ka, s_prev[0]), kay = __fmul_rn(c.ka, s_prev[1]);
+    const float kdx = __fmul_rn(c.kd, s_prev[0]), kdy = __fmul_rn(c.kd, s_prev[1]);
     T2* __restrict__ dst = static_cast<T2*>(a.dst);
     const int NP = (int)(a.ncell / 2), nxp = nx / 2;
 
@@ -195,37 +199,28 @@ __global__ void __launch_bounds__(TmaShape<TMA_R, TMA_NS>::threads)
                 const unsigned char* S[3] = {sm + ((seq + j + 1) % TMA_NS) * TS_BYTES,
                                              sm + ((seq + j) % TMA_NS) * TS_BYTES,
                                              sm + ((seq + j - 1) % TMA_NS) * TS_BYTES};
-                float2 Ps[3][3], Ux[3][3], Uy[3][3];
+                // phi and the velocity factors a (u = a s) of the source windows
+                float2 Ps[3][3], Ax[3][3], Ay[3][3];
                 float2 axo = sp2(0.f), ayo = sp2(0.f);
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
                     stage_window(S[r], TS_P, TS_PL, TS_PR, tp, Ps[r]);
                     if (UK == U_FIELD) {
-                        float2 wx[3], wy[3];
-                        stage_window(S[r], TS_U, TS_UL, TS_UR, tp, wx);
-                        stage_window(S[r], TS_U + TMA_W * 4, TS_UL + 16, TS_UR + 16, tp, wy);
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            Ux[r][k] = mul2(wx[k], sp2(s_prev[0]));
-                            Uy[r][k] = mul2(wy[k], sp2(s_prev[1]));
-                        }
+                        stage_window(S[r], TS_U, TS_UL, TS_UR, tp, Ax[r]);
+                        stage_window(S[r], TS_U + TMA_W * 4, TS_UL + 16, TS_UR + 16, tp, Ay[r]);
                         if (r == 1) {
-                            axo = wx[1];
-                            ayo = wy[1];
+                            axo = Ax[1][1];
+                            ayo = Ay[1][1];
                         }
                     } else if (UK == U_ROW) {
                         const int yr = r == 0 ? (y + 1 == ny ? 0 : y + 1) : (r == 1 ? y : (y == 0 ? ny - 1 : y - 1));
-                        const float ux = __fmul_rn(__ldg(a.ua + yr), s_prev[0]);
-                        const float uy = __fmul_rn(__ldg(a.ua + ny + yr), s_prev[1]);
+                        const float ax = __ldg(a.ua + yr), ay = __ldg(a.ua + ny + yr);
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) Ux[r][k] = sp2(ux), Uy[r][k] = sp2(uy);
+                        for (int k = 0; k < 3; ++k) Ax[r][k] = sp2(ax), Ay[r][k] = sp2(ay);
                         if (r == 1) {
-                            axo = sp2(__ldg(a.ua + y));
-                            ayo = sp2(__ldg(a.ua + ny + y));
+                            axo = sp2(ax);
+                            ayo = sp2(ay);
                         }
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) Ux[r][k] = Uy[r][k] = sp2(0.f);
                     }
                 }
                 // pull and decode f_i = g_i(s) + phi(s) f^eq_i(1, u(s, k-1))
@@ -244,7 +239,15 @@ __global__ void __launch_bounds__(TmaShape<TMA_R, TMA_NS>::threads)
                                                            : gw[tp + 1];
                         w = QuadH<STORE>::as_u(P::join(QuadH<STORE>::as_t2(w), QuadH<STORE>::as_t2(hi)));
                     }
-                    f[i] = fma2(Ps[r][cp], feq_unit_pair(c, i, Ux[r][cp], Uy[r][cp]), P::to_f(QuadH<STORE>::as_t2(w)));
+                    // f^eq_i / phi = w_i + k_i e_i . a s(k - 1)
+                    const int wc = wclass<L>(i), ey = L::ey(i);
+                    float2 e = sp2(wc == 0 ? c.w0 : (wc == 1 ? c.wa : c.wd));
+                    if (UK != U_NONE && wc != 0) {
+                        const float sx = wc == 1 ? kax : kdx, sy = wc == 1 ? kay : kdy;
+                        if (ex != 0) e = fma2(sp2(ex > 0 ? sx : -sx), Ax[r][cp], e);
+                        if (ey != 0) e = fma2(sp2(ey > 0 ? sy : -sy), Ay[r][cp], e);
+                    }
+                    f[i] = fma2(Ps[r][cp], e, P::to_f(QuadH<STORE>::as_t2(w)));
                 }
                 const int cellp = y * nxp + (xs >> 1) + tp;
                 if (WALLS) {
