@@ -137,6 +137,62 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class NvmlPoller:
+    """SM clock and clock-event reasons read through NVML (the driver's library,
+    loaded with ctypes; read-only queries) every ~0.5 ms from a background
+    thread, so that even a timed region of a few milliseconds holds samples.
+    Stays empty where the library or a query is unavailable."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, dev_index: int):
+        self.dev = dev_index
+        self.samples = []      # (time.time(), sm_mhz, reason bits)
+        self.stop = threading.Event()
+        self.t = None
+
+    def __enter__(self):
+        import ctypes
+
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return self
+            h = ctypes.c_void_p()
+            if nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.dev), ctypes.byref(h)) != 0:
+                return self
+            reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        except (OSError, AttributeError):
+            return self
+        mhz = ctypes.c_uint()
+        bits = ctypes.c_ulonglong()
+
+        def poll():
+            while not self.stop.is_set():
+                if nv.nvmlDeviceGetClockInfo(h, ctypes.c_int(1), ctypes.byref(mhz)) == 0 and \
+                        reasons(h, ctypes.byref(bits)) == 0:
+                    self.samples.append((time.time(), float(mhz.value), int(bits.value)))
+                time.sleep(0.0005)
+
+        self.t = threading.Thread(target=poll, daemon=True)
+        self.t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self.stop.set()
+        if self.t:
+            self.t.join(timeout=2)
+
+    def summary(self, window):
+        sel = [x for x in self.samples if window[0] <= x[0] <= window[1]]
+        if not sel:
+            return {"sm_mhz": None, "reasons": [], "samples": 0}
+        reasons = sorted({n for _, _, b in sel for bit, n in self.REASONS.items() if b & bit})
+        return {"sm_mhz": float(np.median([m for _, m, _ in sel])), "reasons": reasons, "samples": len(sel)}
+
+
 def dist_init(args):
     import torch
 
@@ -597,7 +653,7 @@ def main():
     ncell = N_GRID * N_GRID
     barrier(world)
     torch.cuda.synchronize()
-    with ClockSampler(local) as cs:
+    with ClockSampler(local) as cs, NvmlPoller(local) as nvp:
         time.sleep(0.5)                      # let the sampler start
         # The K timed steps sit inside about 1.2 s of identical back-to-back
         # steps (untimed before and after), so that the 100 ms clock sampler
@@ -623,6 +679,11 @@ def main():
     clocks["window"] = ("the timed steps inside about 1.2 s of identical untimed steps before and after "
                         "(samples over that window)")
     clocks["samples_in_timed_steps"] = cs.summary((t_timed0, t_timed1))["samples"]
+    nv_timed = nvp.summary((t_timed0, t_timed1))
+    clocks["timed_steps_nvml"] = dict(nv_timed, note="NVML read every ~0.5 ms inside the timed steps")
+    if nv_timed["samples"]:
+        clocks["samples_in_timed_steps"] = nv_timed["samples"]
+        clocks["reasons"] = sorted(set(clocks["reasons"]) | set(nv_timed["reasons"]))
     if clocks["sm_mhz"]:
         clocks["ms_per_step_x_sm_mhz"] = dt / args.steps * 1e3 * clocks["sm_mhz"]
 
