@@ -354,8 +354,10 @@ typedef struct {
                                 cooperative launch per graph chunk: blocks or warps take work
                                 tiles from a counter, bounded grid barriers separate the step's
                                 phases) / PER_STEP (per step: one launch over 32 x 16 cell
-                                tiles, two nodes per thread in paired FP32 arithmetic, then two
-                                moment passes) */
+                                tiles, two nodes per thread in paired FP32 arithmetic; its two
+                                moment passes run on a second, library-owned stream, overlapping
+                                the next step's cells, and join the batch's stream at the end
+                                of each run) */
     int32_t tile_rows;       /* PERSISTENT work tiles: 0 (default) the 32 x 16 cell tiles of
                                 PER_STEP taken by whole blocks, with the moment passes between
                                 grid barriers inside the launch; 1 .. 1024: tiles of 32 columns
