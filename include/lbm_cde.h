@@ -262,7 +262,9 @@ lbm_status lbm_cde_run_host(lbm_cde_t h, const float* phi0_host, int64_t nsteps,
  * with walls (Eq. 5, Sec. 3.2) and C_k = M^-1 [I - S (I - m^eq(1, u(k)) e_0^T)] M
  * the collision (Eq. 13, 30-31 / A.5). The adjoint mu_k = dL/dB_k obeys
  * mu_{k-1} = P^T C_k^T mu_k. Supported: FP32 storage, periodic / NOFLUX_NODE /
- * BOUNCEBACK walls on any face (LBM_E_UNSUPPORTED otherwise). */
+ * BOUNCEBACK walls on any face and DIRICHLET walls on the y faces, where the
+ * step is affine and its linear part is transposed (velocity gradients are
+ * not formed with DIRICHLET walls); LBM_E_UNSUPPORTED otherwise. */
 
 /* Number of gradient accumulators of one reverse step: 2 dim^2 + q
  * (G_A[dim][dim], G_AC[dim][dim], G_diag[q]; see lbm_cde_grad_rates). */

@@ -446,7 +446,8 @@ def adjoint_gradients(p: Params, phi0, nsteps: int, dL_dphiN, u=None, u_of_t=Non
     The velocity is ``u`` (constant in time) or ``u_of_t(t)``. Returns
     (dL/dphi0 [ncell], dL/dD [dim x dim, entries treated independently],
      dL/du [nsteps][dim x ncell] per collision time t (t = 0 includes the
-     dependence of the initial equilibrium on u(0)), dL/dS [q x q])."""
+     dependence of the initial equilibrium on u(0)), dL/dS [q x q]). With a
+     Dirichlet wall dL/du is not formed (None): the fill's weights depend on u."""
     uf = (lambda t: _u_arr(p, u)) if u_of_t is None else (lambda t: _u_arr(p, u_of_t(t)))
     states = [init_eq(p, phi0, uf(0))]
     post = np.empty_like(states[0])
@@ -455,15 +456,19 @@ def adjoint_gradients(p: Params, phi0, nsteps: int, dL_dphiN, u=None, u_of_t=Non
     lam = np.tile(np.asarray(dL_dphiN, dtype=np.float64).reshape(-1), p.q)
     dS = np.zeros((p.q, p.q))
     du = np.zeros((max(nsteps, 1), p.dim * p.ncell))
+    want_du = DIRICHLET not in (p.bc_lo, p.bc_hi)
     for n in range(nsteps - 1, -1, -1):
-        lam, dSn, dun = adjoint_step(p, lam, states[n], uf(n), want_dS=True, want_du=True)
+        lam, dSn, dun = adjoint_step(p, lam, states[n], uf(n), want_dS=True, want_du=want_du)
         dS += dSn
-        du[n] += dun
+        if want_du:
+            du[n] += dun
     dphi, dfdu = feq_jacobian(p, phi0, uf(0))
     lam2 = lam.reshape(p.q, p.ncell)
     g_phi0 = (lam2 * dphi.reshape(p.q, p.ncell)).sum(axis=0)
     du[0] += (dfdu.reshape(p.dim, p.q, p.ncell) * lam2[None]).sum(axis=1).reshape(-1)
     gD = grad_D_from_s(p, s_gradients(p, dS)) if p.q == 9 else None
+    if not want_du:
+        return g_phi0, gD, None, dS
     if u_of_t is None:
         return g_phi0, gD, du.sum(axis=0).reshape(p.dim, p.ncell), dS
     return g_phi0, gD, du.reshape(-1, p.dim, p.ncell), dS

@@ -679,15 +679,17 @@ static void collision_matrix(const orc_lattice* L, const orc_params* p, const do
  *   du       : += dL/du_a(x, t)             [dim*ncell] (or NULL)
  * The streaming part is the literal transpose of the push + wall rules in
  * orc_step (walls on any face), applied in reverse order; the collision part
- * multiplies by C^T. Dirichlet walls are affine, not linear, and are rejected
- * here. */
+ * multiplies by C^T. A Dirichlet wall makes the step affine; its linear part is
+ * transposed, and velocity partials (du) are not formed with one (-4). */
 int orc_adjoint_step(const orc_params* p, const double* lam_next, const double* f_pre,
                      const double* u, double* lam_out, double* dS, double* du)
 {
     orc_lattice L;
     int rc = build_lattice(&L, p);
     if (rc) return rc;
-    if (p->bc_lo == ORC_DIRICHLET || p->bc_hi == ORC_DIRICHLET) return -4;
+    /* Dirichlet walls: the fill is affine in f; its linear part is transposed below.
+     * Velocity partials through the fill (its weights depend on u) are not formed. */
+    if ((p->bc_lo == ORC_DIRICHLET || p->bc_hi == ORC_DIRICHLET) && du) return -4;
     const int64_t nx = p->nx, ny = p->ny, nz = p->nz, nc = ncells(p);
     const int q = L.q;
     double* lam = (double*)malloc(sizeof(double) * q * nc);  /* adjoint of f(t+1) before wall fill */
@@ -697,6 +699,35 @@ int orc_adjoint_step(const orc_params* p, const double* lam_next, const double* 
     int opp[ORC_MAXQ];
     for (int i = 0; i < q; ++i) opp[i] = opposite(&L, i);
     if (any_wall(p)) {
+        /* transpose of the Dirichlet fill (the last rule of wall_fill): at a wall node
+         * of a DIRICHLET face the inward populations are f_i = phi_s w_i with
+         * w = f^eq(1, u), W = sum of the inward w_i and phi_s = (phi_w - sum of the
+         * other populations) / W, so each other population j receives
+         * -sum_i w_i lam_i / W and the inward ones carry nothing further back */
+        for (int side = 0; side < 2; ++side) {
+            const int kind = side == 0 ? p->bc_lo : p->bc_hi;
+            if (kind != ORC_DIRICHLET) continue;
+            const int64_t y = side == 0 ? 0 : ny - 1;
+            const int inward = side == 0 ? +1 : -1;
+            for (int64_t z = 0; z < nz; ++z)
+                for (int64_t x = 0; x < nx; ++x) {
+                    const int64_t c = x + nx * (y + ny * z);
+                    double uu[3], me[ORC_MAXQ], w[ORC_MAXQ];
+                    get_u(&L, u, nc, c, uu);
+                    meq(&L, p, 1.0, uu, me);
+                    matvec(q, L.Minv, me, w);
+                    double W = 0.0, lw = 0.0;
+                    for (int i = 0; i < q; ++i)
+                        if (L.e[i][1] == inward) {
+                            W += w[i];
+                            lw += w[i] * lam[i * nc + c];
+                        }
+                    for (int i = 0; i < q; ++i) {
+                        if (L.e[i][1] == inward) lam[i * nc + c] = 0.0;
+                        else lam[i * nc + c] -= lw / W;
+                    }
+                }
+        }
         /* transpose of the NOFLUX_NODE fill of wall_fill: at a wall node the
          * populations whose source lies beyond NOFLUX_NODE faces took the value
          * (before the fill) of the population reflected in those axes */

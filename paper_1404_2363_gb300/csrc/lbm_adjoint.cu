@@ -181,8 +181,38 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA && WM < 2) ? 4 : 3) k_a
             for (int i = 0; i < Q; ++i)
                 if (L::ey(i) != 0 && ((L::ey(i) == 1) == lo)) {
                     if (kind == BC_NOFLUX) f[i] = f[mirror_y<L>(i)];
-                    else f[i] = __ldg(a.fprev + (IX)opposite<L>(i) * N + cell);
+                    else if (kind == BC_BOUNCE) f[i] = __ldg(a.fprev + (IX)opposite<L>(i) * N + cell);
                 }
+        }
+        // Dirichlet fill (y faces, wall mode 1 or 2): the inward populations are
+        // phi_s w_i with w = f^eq(1, u(k - 1)) and phi_s from the others (Sec. 3.2)
+        const bool dlo = WM > 0 && y == 0 && a.bc_lo == BC_DIRICHLET;
+        const bool dhi = WM > 0 && y == ny - 1 && a.bc_hi == BC_DIRICHLET;
+        float dw[Q], dW = 1.f;
+        if (dlo || dhi) {
+            float up[3] = {0.f, 0.f, 0.f};
+            float sp[3];
+            sched_row_at(a.sched, a.srow_prev, DIM, sp);
+            if (UK == U_FIELD) {
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) up[d] = __fmul_rn(__ldg(a.ua + (IX)d * N + cell), sp[d]);
+            } else if (UK == U_ROW) {
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) up[d] = __fmul_rn(__ldg(a.ua + d * ny + y), sp[d]);
+            }
+            const int inward = dlo ? 1 : -1;
+            float known = 0.f, wk = 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                dw[i] = feq_unit<L>(c, i, up[0], up[1], up[2]);
+                if (L::ey(i) == inward) wk += dw[i];
+                else known += f[i];
+            }
+            dW = wk;
+            const float ps = ((dlo ? a.phiw_lo : a.phiw_hi) - known) / wk;
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if (L::ey(i) == inward) f[i] = __fmul_rn(ps, dw[i]);
         }
         float ux = 0.f, uy = 0.f, uz = 0.f;
         if (UK == U_FIELD) {
@@ -272,7 +302,19 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA && WM < 2) ? 4 : 3) k_a
 #pragma unroll
         for (int k = 1; k < Q; ++k) g[2 * DIM * DIM + k] = fmaf(-av[k], dm[k], g[2 * DIM * DIM + k]);
 
-        // push nu with the transposed wall rules
+        // push nu with the transposed wall rules; first the Dirichlet fill's: every
+        // other population takes -sum_i w_i nu_i / W over the inward i, which carry
+        // nothing further back
+        if (dlo || dhi) {
+            const int inward = dlo ? 1 : -1;
+            float lw = 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                if (L::ey(i) == inward) lw = fmaf(dw[i], nu[i], lw);
+            const float r = lw / dW;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) nu[i] = L::ey(i) == inward ? 0.f : nu[i] - r;
+        }
         float* out = a.mu_out;
         if constexpr (BOX) {
             float reg[Q], own[Q];
@@ -301,13 +343,13 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA && WM < 2) ? 4 : 3) k_a
             for (int i = 0; i < Q; ++i) {
                 if (L::ey(i) != 0 && ((L::ey(i) == 1) == lo)) {          // entered from beyond the wall
                     if (kind == BC_NOFLUX) nu[mirror_y<L>(i)] += nu[i];
-                    else out[(IX)opposite<L>(i) * N + cell] = nu[i];
+                    else if (kind == BC_BOUNCE) out[(IX)opposite<L>(i) * N + cell] = nu[i];
                 }
             }
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 if (L::ey(i) != 0 && ((L::ey(i) == 1) == lo)) continue;
-                if (kind == BC_NOFLUX && L::ey(i) != 0) out[(IX)i * N + cell] = 0.f;  // left the domain
+                if (kind != BC_BOUNCE && L::ey(i) != 0) out[(IX)i * N + cell] = 0.f;  // left the domain
                 out[(IX)i * N + tgt(i)] = nu[i];
             }
         } else {

@@ -811,8 +811,6 @@ static lbm_status adjoint_supported(lbm_cde_t h)
         return fail(h, LBM_E_UNSUPPORTED, "the adjoint covers the equilibria linear in u (MRT-A, MRT-B3)");
     if (h->d.storage != LBM_STORE_F32)
         return fail(h, LBM_E_UNSUPPORTED, "the adjoint needs FP32 state storage");
-    if (h->d.bc_lo_y == LBM_BC_DIRICHLET || h->d.bc_hi_y == LBM_BC_DIRICHLET)
-        return fail(h, LBM_E_UNSUPPORTED, "the adjoint does not support Dirichlet walls");
     if (!h->d_set) return fail(h, LBM_E_STATE, "set_D must come first");
     return LBM_OK;
 }
@@ -854,6 +852,9 @@ static lbm::AdjArgs make_adj(lbm_cde_t h, int64_t k, const float* mu_in, float* 
     a.sched_len = h->sched_len;
     a.k = k;
     a.srow = lbm::sched_row(k, h->sched ? h->sched_len : 0);
+    a.srow_prev = lbm::sched_row(k - 1, h->sched ? h->sched_len : 0);
+    a.phiw_lo = (float)h->d.phi_w_lo_y;
+    a.phiw_hi = (float)h->d.phi_w_hi_y;
     a.rows = lbm::adjoint_rows(h->d.nx, h->d.ny, h->d.nz, h->sms);
     a.nx = (int)h->d.nx;
     a.ny = (int)h->d.ny;
@@ -882,6 +883,8 @@ lbm_status lbm_cde_adjoint_step(lbm_cde_t h, int64_t k, const float* mu_k_dev, f
     if (s != LBM_OK) return s;
     if (dL_da_dev && h->ukind != LBM_U_FIELD)
         return fail(h, LBM_E_UNSUPPORTED, "velocity gradients need a velocity field (LBM_U_FIELD)");
+    if (dL_da_dev && (h->d.bc_lo_y == LBM_BC_DIRICHLET || h->d.bc_hi_y == LBM_BC_DIRICHLET))
+        return fail(h, LBM_E_UNSUPPORTED, "velocity gradients are not formed with Dirichlet walls");
     s = ensure_adjoint_buffers(h);
     if (s != LBM_OK) return s;
     if (reinterpret_cast<uintptr_t>(grad_acc_dev) % 8 != 0) return fail(h, LBM_E_ARG, "grad_acc_dev not 8-byte aligned");
@@ -1002,6 +1005,8 @@ lbm_status lbm_cde_backward(lbm_cde_t h, const float* dL_dphiN_dev, float* dL_dp
     if (s != LBM_OK) return s;
     if (dL_da_dev && h->ukind != LBM_U_FIELD)
         return fail(h, LBM_E_UNSUPPORTED, "velocity gradients need a velocity field (LBM_U_FIELD)");
+    if (dL_da_dev && (h->d.bc_lo_y == LBM_BC_DIRICHLET || h->d.bc_hi_y == LBM_BC_DIRICHLET))
+        return fail(h, LBM_E_UNSUPPORTED, "velocity gradients are not formed with Dirichlet walls");
     s = ensure_adjoint_buffers(h);
     if (s != LBM_OK) return s;
     const int ng = lbm::adjoint_ngrad(h->q);

@@ -112,6 +112,8 @@ struct AdjArgs {
     long long sched_len;
     long long k;          // the forward step being reversed (collision with u(k))
     int srow;             // k mod sched_len, or -1 without a schedule
+    int srow_prev;        // (k - 1) mod sched_len, or -1: u(k - 1) of the Dirichlet fill
+    float phiw_lo, phiw_hi;   // Dirichlet wall values (y faces)
     int rows;             // grid rows per block (adjoint_rows)
     int nx, ny, nz;
     long long ncell;

@@ -272,6 +272,50 @@ def test_adjoint_with_walls_on_x_and_z_faces(O, case):
             assert abs(an - fd) <= 1e-4 * abs(fd) + 1e-7, (i, j, an, fd)
 
 
+DIRICHLET_ADJ = [
+    Case(nx=70, ny=41, steps=60, bc=("dirichlet", "dirichlet"), phi_w=(1.0, 0.25)),
+    Case(nx=64, ny=33, steps=60, bc=("dirichlet", "noflux"), phi_w=(0.5, 0.0), ukind="row"),
+    Case(nx=37, ny=29, steps=40, bc=("dirichlet", "dirichlet"), phi_w=(1.0, 0.25), bc_x=("noflux", "bounceback")),
+]
+
+
+@pytest.mark.parametrize("case", DIRICHLET_ADJ, ids=lambda c: f"{c.bc[0]}-{c.bc[1]}-x{c.bc_x[0]}-{c.ukind}")
+def test_adjoint_with_dirichlet_walls(O, case):
+    """Dirichlet walls (Sec. 3.2) make the step affine; the reverse-time kernels
+    transpose its linear part (the fill's weights w = f^eq(1, u(k - 1)) at the
+    wall node), in the y-wall mode and, with walls on the x faces too, in the box
+    mode: dL/dphi0 and dL/dD against the FP64 oracle adjoint, whose Dirichlet
+    transpose is pinned against the assembled step (tests/test_oracle_adjoint.py).
+    Velocity gradients are not formed with Dirichlet walls (LBM_E_UNSUPPORTED)."""
+    from paper_1404_2363_gb300 import _native as N
+
+    phi0, a, sched = case.inputs()
+    g = np.random.default_rng(9).standard_normal(case.shape)
+    s = Solver(nx=case.nx, ny=case.ny, bc=case.bc, bc_x=case.bc_x, phi_w=case.phi_w)
+    s.set_D(case.D)
+    if a is not None:
+        s.set_velocity(torch.from_numpy(a).cuda(), None if sched is None else torch.from_numpy(sched).cuda(),
+                       kind="row" if case.ukind == "row" else "field")
+    s.forward_ckpt(torch.from_numpy(phi0).cuda(), case.steps)
+    dphi0, dD, _, _ = s.backward(torch.from_numpy(g.astype(np.float32)).cuda(), want_da=False)
+    if case.ukind == "field":
+        with pytest.raises(N.LbmError) as e:
+            s.backward(torch.from_numpy(g.astype(np.float32)).cuda(), want_da=True)
+        assert e.value.status == N.LBM_E_UNSUPPORTED
+    s.close()
+    wp, wD, _ = oracle_grads(O, case, phi0, None, sched, g) if case.ukind == "none" else \
+        _oracle_grads_nou(O, case, phi0, a, sched, g)
+    assert rel_l2(dphi0.cpu().numpy().astype(np.float64), wp) < 1e-5
+    assert np.abs(dD - wD).max() <= 1e-4 * np.abs(wD).max()
+
+
+def _oracle_grads_nou(O, case, phi0, a, sched, g):
+    p = oracle_params(O, case)
+    gp, gD, _, _ = O.adjoint_gradients(p, phi0.astype(np.float64).reshape(-1), case.steps, g.reshape(-1),
+                                       u_of_t=case.u_of_t(a, sched))
+    return gp.reshape(case.shape), gD, None
+
+
 def test_single_step_api_matches_backward():
     """lbm_cde_adjoint_step driven step by step from the host (forward states kept
     with get_state, compensated FP32 gradient accumulators) gives the same dL/dD

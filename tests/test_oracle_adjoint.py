@@ -42,6 +42,35 @@ def test_adjoint_step_is_transpose(O, bc, model):
         assert np.abs(T.sum(axis=0) - 1.0).max() < 1e-13
 
 
+@pytest.mark.parametrize("bx", [("periodic", "periodic"), ("noflux", "bounceback")])
+def test_adjoint_step_is_transpose_with_dirichlet_walls(O, bx):
+    """Dirichlet walls (Sec. 3.2, wall-node phi_w) make the step affine,
+    f(t+1) = T f(t) + b: the adjoint step equals T^T of its linear part, the
+    constant b (from phi_w) being removed by taking differences; alone and
+    meeting walls on the x faces."""
+    K = {"periodic": O.PERIODIC, "noflux": O.NOFLUX_NODE, "bounceback": O.BOUNCEBACK}
+    nx, ny = 4, 5
+    p = O.Params(nx=nx, ny=ny, A=O.A_from_D(W.D_ANISO), bc_lo=O.DIRICHLET, bc_hi=O.DIRICHLET,
+                 phi_w_lo=1.0, phi_w_hi=0.25, bcx_lo=K[bx[0]], bcx_hi=K[bx[1]])
+    g = np.random.default_rng(12)
+    u = g.uniform(-0.05, 0.05, (2, nx * ny))
+    n = 9 * nx * ny
+    post = np.empty(n)
+    b = O.step(p, np.zeros(n), u, post)
+    T = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        T[:, j] = O.step(p, e, u, post) - b
+    assert np.abs(b).max() > 0.01            # the walls do add a constant
+    lam = g.standard_normal(n)
+    f = g.standard_normal(n)
+    got, _, _ = O.adjoint_step(p, lam, f, u)
+    assert np.abs(got - T.T @ lam).max() < 1e-12
+    with pytest.raises(RuntimeError):
+        O.adjoint_step(p, lam, f, u, want_du=True)   # velocity partials: not with Dirichlet
+
+
 BOXES = [
     # (lattice, x faces, y faces, z faces)
     (9, ("noflux", "noflux"), ("periodic", "periodic"), None),
