@@ -121,8 +121,12 @@ def max_threads() -> int:
 # Parameters
 # ---------------------------------------------------------------------------
 
-def diffusion_factor(q: int, alpha1: float, alpha2: float) -> float:
-    """The scalar k in D = k dt (I - A/2) A^-1: Eq. 36 for D2Q9, Eq. A.6 for D3Q15."""
+def diffusion_factor(q: int, alpha1: float, alpha2: float, model: int = MRT_A) -> float:
+    """The scalar k in D = k dt (I - A/2) A^-1: Eq. 36 for D2Q9, Eq. A.6 for D3Q15.
+    The unmodified D2Q9 models MRT-B1/B2/B3 (Sec. 3.1, after Eq. 39) all give
+    k = 1/3, whatever constants their equilibria carry."""
+    if q == 9 and model != MRT_A:
+        return 1.0 / 3.0
     if q == 9:
         return 2.0 / 3.0 + alpha1 / 8.0 + alpha2 / 12.0
     return 2.0 / 3.0 + 55.0 / 54.0 * alpha1 + alpha2 / 216.0
@@ -370,7 +374,7 @@ def grad_D_from_s(p: Params, gs: dict) -> np.ndarray:
     """dL/dD for the parametrisation A = (D/k + I/2)^-1 with s4 = sxx, s6 = syy
     (tie) and S symmetric in the off-diagonal block (sxy = syx = A01)."""
     A = np.asarray(p.A, dtype=np.float64)
-    k = diffusion_factor(p.q, p.alpha1, p.alpha2)
+    k = diffusion_factor(p.q, p.alpha1, p.alpha2, p.model)
     GA = np.array([[gs["sxx"] + (gs["s4"] if p.tie else 0.0), gs["sxy"]],
                    [gs["syx"], gs["syy"] + (gs["s6"] if p.tie else 0.0)]])
     # dA = -A (dD / k) A  =>  dL/dD = -(1/k) A^T GA A^T

@@ -109,9 +109,9 @@ def test_adjoint_step_is_transpose_with_walls_on_any_face(O, lattice, bx, by, bz
         assert np.abs(T.sum(axis=0) - 1.0).max() < 1e-12   # bounce-back conserves mass
 
 
-def misfit_setup(O, nx=8, ny=7, bc="periodic"):
+def misfit_setup(O, nx=8, ny=7, bc="periodic", model=0):
     kind = {"periodic": O.PERIODIC, "noflux": O.NOFLUX_NODE}[bc]
-    p = O.Params(nx=nx, ny=ny, bc_lo=kind, bc_hi=kind, A=O.A_from_D(W.D_ANISO))
+    p = O.Params(nx=nx, ny=ny, bc_lo=kind, bc_hi=kind, A=O.A_from_D(W.D_ANISO), model=model)
     phi0, u = W.random_fields(nx, ny, seed=6)
     obs = np.random.default_rng(9).uniform(0.5, 1.5, nx * ny)
     return p, phi0.reshape(-1), u.reshape(2, -1), obs
@@ -122,10 +122,12 @@ def loss(O, p, phi0, u, obs, nsteps):
     return 0.5 * float(((phi - obs) ** 2).sum()), phi
 
 
-@pytest.mark.parametrize("bc", ["periodic", "noflux"])
-def test_gradients_match_central_differences(O, bc):
+@pytest.mark.parametrize("bc,model", [("periodic", 0), ("noflux", 0), ("periodic", 1), ("noflux", 2)])
+def test_gradients_match_central_differences(O, bc, model):
+    """MRT-B1/B2 (model 1, 2) carry u^2 terms in m^eq (Eq. 38-39) and the
+    unmodified S: their velocity and D gradients take other paths."""
     nsteps = 12
-    p, phi0, u, obs = misfit_setup(O, bc=bc)
+    p, phi0, u, obs = misfit_setup(O, bc=bc, model=model)
     L0, phiN = loss(O, p, phi0, u, obs, nsteps)
     g_phi0, gD, g_u, _ = O.adjoint_gradients(p, phi0, nsteps, phiN - obs, u=u)
     D = W.D_ANISO.copy()
