@@ -261,10 +261,12 @@ lbm_status lbm_cde_run_host(lbm_cde_t h, const float* phi0_host, int64_t nsteps,
  * B_k = C_k P B_{k-1} with B the stored post-collision state, P the pull-stream
  * with walls (Eq. 5, Sec. 3.2) and C_k = M^-1 [I - S (I - m^eq(1, u(k)) e_0^T)] M
  * the collision (Eq. 13, 30-31 / A.5). The adjoint mu_k = dL/dB_k obeys
- * mu_{k-1} = P^T C_k^T mu_k. Supported: FP32 storage, periodic / NOFLUX_NODE /
- * BOUNCEBACK walls on any face and DIRICHLET walls on the y faces, where the
- * step is affine and its linear part is transposed (velocity gradients are
- * not formed with DIRICHLET walls); LBM_E_UNSUPPORTED otherwise. */
+ * mu_{k-1} = P^T C_k^T mu_k. Supported: FP32 storage, every model (MRT-A and
+ * the MRT-B1/B2/B3 of Eq. 37-39, whose u^2 equilibrium terms enter dL/du),
+ * periodic / NOFLUX_NODE / BOUNCEBACK walls on any face and DIRICHLET walls on
+ * the y faces, where the step is affine and its linear part is transposed
+ * (velocity gradients are not formed with DIRICHLET walls); LBM_E_UNSUPPORTED
+ * otherwise. */
 
 /* Number of gradient accumulators of one reverse step: 2 dim^2 + q
  * (G_A[dim][dim], G_AC[dim][dim], G_diag[q]; see lbm_cde_grad_rates). */
@@ -292,8 +294,9 @@ lbm_status lbm_cde_adjoint_step(lbm_cde_t h, int64_t k, const float* mu_k_dev, f
 /* Converts accumulated partials g (host, lbm_cde_adjoint_ngrad doubles) into
  * dL/dD (host, dim x dim, every entry an independent variable; includes the
  * tied rates s4 = sxx ... when tie_q_rates = 1) through A = (D/k + I/2)^-1, and
- * dL/ds (host [15], the diagonal rates as independent variables). Either output
- * may be NULL. */
+ * dL/ds (host [15], the diagonal rates as independent variables). For the
+ * MRT-B models S has no coupling entries (Eq. 24) and G_AC is not used. Either
+ * output may be NULL. */
 lbm_status lbm_cde_grad_rates(lbm_cde_t h, const double* g, double* dL_dD_host, double* dL_ds_host);
 
 /* Forward run for differentiation: f(0) = f^eq(phi0, u(0)), nsteps steps, keeping

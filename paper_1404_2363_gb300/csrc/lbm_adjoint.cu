@@ -241,6 +241,15 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA && WM < 2) ? 4 : 3) k_a
             v[3 + 2 * d] = u[d];
             v[4 + 2 * d] = -u[d];
         }
+        // MRT-B1/B2 (D2Q9, Eq. 38-39): the u^2 terms of m^eq (c.b1 = c.g7 = 0 otherwise)
+        const bool quad = L::Q == 9 && (c.b1 != 0.f || c.g7 != 0.f);
+        if (quad) {
+            const float u2 = fmaf(ux, ux, uy * uy);
+            v[1] = fmaf(c.b1, u2, c.meq1);
+            v[2] = fmaf(c.b2, u2, c.meq2);
+            v[7] = c.g7 * fmaf(ux, ux, -uy * uy);
+            v[8] = c.g8 * (ux * uy);
+        }
         float dm[Q];
 #pragma unroll
         for (int k = 1; k < Q; ++k) dm[k] = fmaf(-phi, v[k], m[k]);
@@ -279,9 +288,16 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA && WM < 2) ? 4 : 3) k_a
 
         // velocity partials: u(x, k) = a(x) s(k)  =>  dL/da += s(k) dL/du(k)
         if (DA) {
+            float gu[DIM];   // dL/du(k) / phi = b . dv/du
 #pragma unroll
-            for (int d = 0; d < DIM; ++d)
-                a.du_acc[(IX)d * N + cell] = du_old[d] + phi * (b[3 + 2 * d] - b[4 + 2 * d]) * s_now[d];
+            for (int d = 0; d < DIM; ++d) gu[d] = b[3 + 2 * d] - b[4 + 2 * d];
+            if (quad) {
+                const float q12 = fmaf(c.b1, b[1], c.b2 * b[2]);
+                gu[0] += fmaf(2.f * ux, fmaf(c.g7, b[7], q12), c.g8 * uy * b[8]);
+                gu[1] += fmaf(2.f * uy, fmaf(-c.g7, b[7], q12), c.g8 * ux * b[8]);
+            }
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) a.du_acc[(IX)d * N + cell] = du_old[d] + phi * gu[d] * s_now[d];
         } else if (UK == U_FIELD && a.du_acc != nullptr) {
             // never taken (gradient buffers go to the DA instance); kept because this
             // instance measured faster with it (register allocation)
@@ -438,14 +454,35 @@ __global__ void k_adjoint_init(const AdjArgs a, const float* __restrict__ phi0, 
         float ux, uy, uz;
         vel_at_p<UK, L::DIM>(a.ua, a.ncell, a.ny, c, y, s0, ux, uy, uz);
         float gp = 0.f, gu[3] = {0.f, 0.f, 0.f};
+        if (L::Q == 9 && (a.c.b1 != 0.f || a.c.g7 != 0.f)) {
+            // MRT-B1/B2 (Eq. 38-39): f^eq = M^T diag(1/|M_k|^2) m^eq(phi, u) carries u^2
+            // terms, so dL/du = phi0 beta . dm^eq/du with beta = diag(1/|M_k|^2) M mu_0
+            float mu[L::Q], fe[L::Q], bt[L::Q];
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-            const float m = __ldg(a.mu_in + (long long)i * a.ncell + c);
-            gp = fmaf(m, feq_unit<L>(a.c, i, ux, uy, uz), gp);
-            const float k = wclass<L>(i) == 1 ? a.c.ka : (wclass<L>(i) == 2 ? a.c.kd : 0.f);
-            gu[0] = fmaf(m * k, (float)L::ex(i), gu[0]);
-            gu[1] = fmaf(m * k, (float)L::ey(i), gu[1]);
-            gu[2] = fmaf(m * k, (float)L::ez(i), gu[2]);
+            for (int i = 0; i < L::Q; ++i) mu[i] = __ldg(a.mu_in + (long long)i * a.ncell + c);
+            feq_full<L>(a.c, 1.f, ux, uy, uz, fe);
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) gp = fmaf(mu[i], fe[i], gp);
+#pragma unroll
+            for (int k = 0; k < L::Q; ++k) {
+                float acc = 0.f;
+#pragma unroll
+                for (int i = 0; i < L::Q; ++i) acc = fmaf((float)L::M(k, i), mu[i], acc);
+                bt[k] = acc * (1.0f / (float)row_norm2<L>(k));
+            }
+            const float q12 = fmaf(a.c.b1, bt[1], a.c.b2 * bt[2]);
+            gu[0] = bt[3] - bt[4] + fmaf(2.f * ux, fmaf(a.c.g7, bt[7], q12), a.c.g8 * uy * bt[8]);
+            gu[1] = bt[5] - bt[6] + fmaf(2.f * uy, fmaf(-a.c.g7, bt[7], q12), a.c.g8 * ux * bt[8]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                const float m = __ldg(a.mu_in + (long long)i * a.ncell + c);
+                gp = fmaf(m, feq_unit<L>(a.c, i, ux, uy, uz), gp);
+                const float k = wclass<L>(i) == 1 ? a.c.ka : (wclass<L>(i) == 2 ? a.c.kd : 0.f);
+                gu[0] = fmaf(m * k, (float)L::ex(i), gu[0]);
+                gu[1] = fmaf(m * k, (float)L::ey(i), gu[1]);
+                gu[2] = fmaf(m * k, (float)L::ez(i), gu[2]);
+            }
         }
         dphi0[c] = gp;
         if (UK == U_FIELD && a.du_acc != nullptr) {

@@ -807,8 +807,6 @@ int32_t lbm_cde_adjoint_ngrad(int32_t lattice) { return lbm::adjoint_ngrad(latti
 
 static lbm_status adjoint_supported(lbm_cde_t h)
 {
-    if (h->d.model == LBM_MRT_B1 || h->d.model == LBM_MRT_B2)
-        return fail(h, LBM_E_UNSUPPORTED, "the adjoint covers the equilibria linear in u (MRT-A, MRT-B3)");
     if (h->d.storage != LBM_STORE_F32)
         return fail(h, LBM_E_UNSUPPORTED, "the adjoint needs FP32 state storage");
     if (!h->d_set) return fail(h, LBM_E_STATE, "set_D must come first");
@@ -904,12 +902,14 @@ lbm_status lbm_cde_grad_rates(lbm_cde_t h, const double* g, double* dL_dD_host, 
     double s[15];
     for (int k = 0; k < 15; ++k) s[k] = h->coef.s[k];
     double dA[9] = {0}, ds[15] = {0};
-    // S entries (Eq. 30-31 / A.5): A_ab, C_ab = (A_ab/2 - delta_ab) s_{q_b}, diagonal s_k
+    // S entries (Eq. 30-31 / A.5): A_ab, C_ab = (A_ab/2 - delta_ab) s_{q_b}, diagonal s_k.
+    // The MRT-B models keep the unmodified S of Eq. 24 (C = 0): no coupling term.
+    const bool coupled = h->d.model == LBM_MRT_A;
     for (int a = 0; a < n; ++a)
         for (int b = 0; b < n; ++b) {
             const double sq = s[4 + 2 * b];
-            dA[a * n + b] = GA[a * n + b] + GAC[a * n + b] * sq / 2.0;
-            ds[4 + 2 * b] += GAC[a * n + b] * (h->A[a * n + b] / 2.0 - (a == b ? 1.0 : 0.0));
+            dA[a * n + b] = GA[a * n + b] + (coupled ? GAC[a * n + b] * sq / 2.0 : 0.0);
+            if (coupled) ds[4 + 2 * b] += GAC[a * n + b] * (h->A[a * n + b] / 2.0 - (a == b ? 1.0 : 0.0));
         }
     for (int k = 1; k < q; ++k) {
         const bool flux = (k == 3 || k == 5 || (n == 3 && k == 7));

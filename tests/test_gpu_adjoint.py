@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 
 def gpu_grads(case, phi0, a, sched, g, every=0):
-    s = Solver(nx=case.nx, ny=case.ny, bc=case.bc)
+    s = Solver(nx=case.nx, ny=case.ny, bc=case.bc, model=case.model)
     s.set_D(case.D)
     if a is not None:
         s.set_velocity(torch.from_numpy(a).cuda(), None if sched is None else torch.from_numpy(sched).cuda())
@@ -49,10 +49,16 @@ CASES = [
     Case(nx=70, ny=41, steps=60, bc=("bounceback", "bounceback")),
     Case(nx=64, ny=33, steps=60, bc=("noflux", "noflux"), ukind="row"),
     Case(nx=64, ny=32, steps=40, ukind="none", sched=False),
+    # MRT-B1/B2: m^eq with u^2 terms (Eq. 38-39), unmodified S; MRT-B3: Eq. 37
+    Case(nx=70, ny=40, steps=60, model="B1"),
+    Case(nx=70, ny=41, steps=60, bc=("noflux", "noflux"), model="B2"),
+    Case(nx=64, ny=33, steps=60, bc=("bounceback", "bounceback"), ukind="row", model="B1"),
+    Case(nx=70, ny=40, steps=60, sched=False, model="B3"),
 ]
 
 
-@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c.bc[0]}-{c.ukind}-{'sched' if c.sched else 'const'}")
+@pytest.mark.parametrize("case", CASES,
+                         ids=lambda c: f"{c.model}-{c.bc[0]}-{c.ukind}-{'sched' if c.sched else 'const'}")
 def test_adjoint_matches_fp64_oracle_adjoint(O, case):
     phi0, a, sched = case.inputs()
     g = np.random.default_rng(5).standard_normal(case.shape)
@@ -67,7 +73,7 @@ def test_adjoint_matches_fp64_oracle_adjoint(O, case):
 
 
 def _gpu_nofield(case, phi0, a, sched, g):
-    s = Solver(nx=case.nx, ny=case.ny, bc=case.bc)
+    s = Solver(nx=case.nx, ny=case.ny, bc=case.bc, model=case.model)
     s.set_D(case.D)
     if a is not None:
         s.set_velocity(torch.from_numpy(a).cuda(), None if sched is None else torch.from_numpy(sched).cuda(),
@@ -225,10 +231,12 @@ BOX_ADJ = [
     Case(lattice=15, nx=12, ny=10, nz=9, steps=20, bc=("noflux", "noflux"), bc_x=("bounceback", "bounceback"),
          bc_z=("noflux", "bounceback"),
          D=np.array([[0.03, 0.004, -0.003], [0.004, 0.025, 0.002], [-0.003, 0.002, 0.035]])),
+    Case(nx=37, ny=29, steps=40, bc=("bounceback", "noflux"), bc_x=("noflux", "bounceback"), model="B2"),
 ]
 
 
-@pytest.mark.parametrize("case", BOX_ADJ, ids=lambda c: f"q{c.lattice}-x{c.bc_x[0]}-{c.bc_x[1]}-y{c.bc[0]}-{c.ukind}")
+@pytest.mark.parametrize("case", BOX_ADJ,
+                         ids=lambda c: f"q{c.lattice}-{c.model}-x{c.bc_x[0]}-{c.bc_x[1]}-y{c.bc[0]}-{c.ukind}")
 def test_adjoint_with_walls_on_x_and_z_faces(O, case):
     """Walls on the x (and z) faces, meeting the y walls at edges and corners:
     the reverse-time kernel's wall mode 2 (each pull source found as in the
@@ -238,7 +246,7 @@ def test_adjoint_with_walls_on_x_and_z_faces(O, case):
     phi0, a, sched = case.inputs()
     g = np.random.default_rng(8).standard_normal(case.shape)
     s = Solver(lattice=case.lattice, nx=case.nx, ny=case.ny, nz=case.nz, bc=case.bc, bc_x=case.bc_x,
-               bc_z=case.bc_z or ("periodic", "periodic"))
+               bc_z=case.bc_z or ("periodic", "periodic"), model=case.model)
     s.set_D(case.D)
     if a is not None:
         s.set_velocity(torch.from_numpy(a).cuda(), None if sched is None else torch.from_numpy(sched).cuda(),
