@@ -291,10 +291,12 @@ __global__ void __launch_bounds__(256, 4) k_batch_persistent(const BatchArgs a)
 // writes the tile's 32 column sums of w_y phi.
 // One 32 x 16 cell tile (tile lt of instance I) of step k: the body of
 // k_batch_cells and of the cell-tile persistent kernel. Block-wide (256
-// threads, one barrier); writes the tile's 32 column sums of w_y phi to strip_out.
+// threads, one barrier); writes the tile's 32 column sums of w_y phi to
+// strip_out through the shared rows cs, which the caller does not touch again
+// before the next block-wide barrier (the persistent kernel alternates two).
 template <typename IX>
 __device__ __forceinline__ void cell_tile(const InstK& I, int lt, long long k, float* const (&buf)[2], long long ncat,
-                                          float* __restrict__ strip_out)
+                                          float* __restrict__ strip_out, float (&cs)[8][32])
 {
     const int nx = I.nx, ny = I.ny;
     const int ty = lt / I.tx;
@@ -350,7 +352,6 @@ __device__ __forceinline__ void cell_tile(const InstK& I, int lt, long long k, f
 #pragma unroll
             for (int i = 0; i < 9; ++i) dst[(IX)i * N + cell] = h ? v[i].y : v[i].x;
         }
-    __shared__ float cs[8][32];
     const float pa = live[0] ? (wall[0] ? __fmul_rn(0.5f, phi.x) : phi.x) : 0.f;
     const float pb = live[1] ? (wall[1] ? __fmul_rn(0.5f, phi.y) : phi.y) : 0.f;
     cs[wy][lane] = pa + pb;
@@ -361,7 +362,6 @@ __device__ __forceinline__ void cell_tile(const InstK& I, int lt, long long k, f
         for (int r = 1; r < 8; ++r) sum += cs[r][lane];
         strip_out[lane] = sum;
     }
-    __syncthreads();   // cs is free again for the block's next tile
 }
 
 template <typename IX>
@@ -375,7 +375,8 @@ __global__ void __launch_bounds__(256) k_batch_cells(const __grid_constant__ Cel
         else hi = mid - 1;
     }
     const InstK& I = a.inst[lo];
-    cell_tile<IX>(I, t - I.tile0, *a.kdev + 1 + a.koff, a.buf, a.ncat, a.strip + (long long)(a.tile_base + t) * 32);
+    __shared__ float cs[8][32];
+    cell_tile<IX>(I, t - I.tile0, *a.kdev + 1 + a.koff, a.buf, a.ncat, a.strip + (long long)(a.tile_base + t) * 32, cs);
 }
 
 // Eq. 47 moments of step k for PER_STEP mode, two deterministic passes.
@@ -461,9 +462,12 @@ __global__ void __launch_bounds__(256) k_batch_inst_moments(const BatchArgs a, c
 
 // PERSISTENT mode on cell tiles (tile height 0): one cooperative launch runs
 // the steps of a chunk; each step, the blocks walk the 32 x 16 cell tiles and
-// run the PER_STEP arithmetic (two nodes per thread, paired FP32),
-// then - separated by bounded grid barriers - the column-moment pass over the
-// 256-column blocks and the per-instance sums, as the PER_STEP launches do.
+// run the PER_STEP arithmetic (two nodes per thread, paired FP32). The two
+// moment passes are pipelined behind the cells, so that one bounded grid
+// barrier per step suffices: ahead of the cells of step k the grid runs the
+// column-moment pass of step k - 1 and the per-instance sums of step k - 2
+// (column sums and block partials alternate between two buffers by step
+// parity); after the last step, one more barrier separates the last two passes.
 // The instance constants travel by value in the kernel parameters, as for
 // k_batch_cells (so at most CELL_INST instances), and every read of them is
 // uniform over a block.
@@ -471,34 +475,51 @@ struct PersistArgs {
     BatchArgs b;
     const int* tile_inst; // instance of every cell tile
     int nctiles;          // cell tiles in all
-    float* strip;
+    float* strip[2];      // column sums of the even / odd steps of the launch
     const int* cblk_inst;
     int ncblk;
-    double* cpart;
+    double* cpart[2];     // block partials of the even / odd steps
     int ninst;
     InstK inst[CELL_INST];   // tile0 = the instance's first cell tile
 };
 
 template <typename IX>
-__global__ void __launch_bounds__(256, 5) k_batch_persistent_cells(const __grid_constant__ PersistArgs p)
+__global__ void __launch_bounds__(256, 4) k_batch_persistent_cells(const __grid_constant__ PersistArgs p)
 {
     const BatchArgs& a = p.b;
+    __shared__ float cs[2][8][32];
     const long long t0 = *a.kdev;
+    const int gw = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)(((long long)gridDim.x * blockDim.x) >> 5);
     for (int s = 0; s < a.nsteps; ++s) {
         const long long k = t0 + 1 + s;
+        // step k - 1: its column sums are complete (barrier of the last iteration)
+        if (s >= 1)
+            for (int blk = blockIdx.x; blk < p.ncblk; blk += gridDim.x)
+                col_moments(a, k - 1, blk, p.strip[(s - 1) & 1], p.cblk_inst, p.cpart[(s - 1) & 1]);
+        // step k - 2: its block partials were written before that barrier
+        if (s >= 2)
+            for (int i = gw; i < a.ninst; i += nw) inst_moments(a, k - 2, i, p.cpart[s & 1]);
         // cell tiles blockIdx.x, blockIdx.x + gridDim.x, ...: equal tiles, so the
-        // static split is even to one tile, and no block waits on a counter
-        for (int t = blockIdx.x; t < p.nctiles; t += gridDim.x) {
+        // static split is even to one tile, and no block waits on a counter; the
+        // column-sum rows alternate by tile (one block-wide barrier per tile)
+        float* strip = p.strip[s & 1];
+        int j = 0;
+        for (int t = blockIdx.x; t < p.nctiles; t += gridDim.x, ++j) {
             const InstK& I = p.inst[p.tile_inst[t]];
-            cell_tile<IX>(I, t - I.tile0, k, a.buf, a.ncat, p.strip + (long long)t * 32);
+            cell_tile<IX>(I, t - I.tile0, k, a.buf, a.ncat, strip + (long long)t * 32, cs[j & 1]);
         }
         if (!grid_barrier(a)) return;
-        for (int blk = blockIdx.x; blk < p.ncblk; blk += gridDim.x) col_moments(a, k, blk, p.strip, p.cblk_inst, p.cpart);
-        if (!grid_barrier(a)) return;
-        const int gw = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-        const int nw = (int)(((long long)gridDim.x * blockDim.x) >> 5);
-        for (int i = gw; i < a.ninst; i += nw) inst_moments(a, k, i, p.cpart);
     }
+    const int n = a.nsteps;
+    if (n < 1) return;
+    const long long kl = t0 + n;
+    for (int blk = blockIdx.x; blk < p.ncblk; blk += gridDim.x)
+        col_moments(a, kl, blk, p.strip[(n - 1) & 1], p.cblk_inst, p.cpart[(n - 1) & 1]);
+    if (n >= 2)
+        for (int i = gw; i < a.ninst; i += nw) inst_moments(a, kl - 1, i, p.cpart[n & 1]);
+    if (!grid_barrier(a)) return;
+    for (int i = gw; i < a.ninst; i += nw) inst_moments(a, kl, i, p.cpart[(n - 1) & 1]);
 }
 
 __global__ void k_batch_advance(long long* kdev, int n)
@@ -579,10 +600,12 @@ static cudaError_t launch_mode(int mode, int rows, const BatchArgs& a, const Ins
             p.b = a;
             p.tile_inst = tile_inst;
             p.nctiles = nctiles;
-            p.strip = strip;
+            p.strip[0] = strip;
+            p.strip[1] = ss.strip2;
             p.cblk_inst = cblk_inst;
             p.ncblk = ncblk;
-            p.cpart = cpart;
+            p.cpart[0] = cpart;
+            p.cpart[1] = cpart + 3LL * ncblk;
             p.ninst = ninst;
             for (int i = 0; i < ninst; ++i) p.inst[i] = cinst[i];
             void* args[] = {(void*)&p};
@@ -663,7 +686,7 @@ struct lbm_cde_batch_s {
     lbm::StepStreams ss{};              // PER_STEP: moment stream, events, odd-step column sums
     int* cblk_inst = nullptr;           // instance of each 256-column block of the moment pass
     int ncblk = 0;
-    double* cpart = nullptr;            // [ncblk][3] moment partials
+    double* cpart = nullptr;            // [2][ncblk][3] moment partials (PER_STEP uses the first)
     cudaStream_t st = nullptr;
     std::string err;
 };
@@ -947,7 +970,7 @@ lbm_status lbm_cde_batch_create(const lbm_cde_channel_desc* descs, int32_t n, co
     }
     b->ncblk = (int)(b->inst[n - 1].cblk0 + b->inst[n - 1].ncblk);
     b->cblk_inst = static_cast<int*>(balloc(b, sizeof(int) * (size_t)b->ncblk));
-    b->cpart = static_cast<double*>(balloc(b, sizeof(double) * 3 * (size_t)b->ncblk));
+    b->cpart = static_cast<double*>(balloc(b, sizeof(double) * 6 * (size_t)b->ncblk));   // two parities
     if (!b->inst_dev || !b->buf[0] || !b->buf[1] || !b->sync || !b->moments || !b->strip || !b->ss.strip2 ||
         !b->cblk_inst ||
         !b->cpart) {
