@@ -442,7 +442,8 @@ __global__ void k_grad_sum3(const float2* __restrict__ p2, int ng, float2* __res
 }
 
 // Gradients through the initial state B_0 = f^eq(phi0, u(0)):
-//   dL/dphi0 = sum_i mu_0,i f^eq_i(1, u),   dL/da += s(0) phi0 sum_i mu_0,i k_i e_i
+//   dL/dphi0 = sum_i mu_0,i f^eq_i(1, u),   dL/da += s(0) phi0 sum_i mu_0,i d f^eq_i(1, u) / du
+// (= k_i e_i for the equilibria linear in u; MRT-B1/B2 add their u^2 terms)
 template <class L, int UK>
 __global__ void k_adjoint_init(const AdjArgs a, const float* __restrict__ phi0, float* __restrict__ dphi0)
 {
