@@ -510,6 +510,7 @@ def batch_bench(steps: int):
     def timed(nsteps):
         b.set_phi(phis)
         b.run(64, moments=False)
+        b.run(64, moments=True)   # the timed path itself, once untimed
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()

@@ -290,13 +290,11 @@ __global__ void __launch_bounds__(256, 4) k_batch_persistent(const BatchArgs a)
 // evaluates both collisions in paired FP32 arithmetic (lbm_pair.cuh); warp 0
 // writes the tile's 32 column sums of w_y phi.
 // One 32 x 16 cell tile (tile lt of instance I) of step k: the body of
-// k_batch_cells and of the cell-tile persistent kernel. Block-wide (256
-// threads, one barrier); writes the tile's 32 column sums of w_y phi to
-// strip_out through the shared rows cs, which the caller does not touch again
-// before the next block-wide barrier (the persistent kernel alternates two).
+// k_batch_cells and of the cell-tile persistent kernel. Returns the thread's
+// part of its column sum of w_y phi (its two nodes); the callers add the eight
+// parts of a column through shared memory.
 template <typename IX>
-__device__ __forceinline__ void cell_tile(const InstK& I, int lt, long long k, float* const (&buf)[2], long long ncat,
-                                          float* __restrict__ strip_out, float (&cs)[8][32])
+__device__ __forceinline__ float cell_tile(const InstK& I, int lt, long long k, float* const (&buf)[2], long long ncat)
 {
     const int nx = I.nx, ny = I.ny;
     const int ty = lt / I.tx;
@@ -354,14 +352,51 @@ __device__ __forceinline__ void cell_tile(const InstK& I, int lt, long long k, f
         }
     const float pa = live[0] ? (wall[0] ? __fmul_rn(0.5f, phi.x) : phi.x) : 0.f;
     const float pb = live[1] ? (wall[1] ? __fmul_rn(0.5f, phi.y) : phi.y) : 0.f;
-    cs[wy][lane] = pa + pb;
-    __syncthreads();
-    if (wy == 0) {
-        float sum = cs[0][lane];
+    return pa + pb;
+}
+
+// Column sum of the tile's eight row parts (warp 0, in row order)
+__device__ __forceinline__ void tile_column_sum(const float (&cs)[8][32], float* __restrict__ strip_out)
+{
+    const int lane = threadIdx.x & 31;
+    float sum = cs[0][lane];
 #pragma unroll
-        for (int r = 1; r < 8; ++r) sum += cs[r][lane];
-        strip_out[lane] = sum;
-    }
+    for (int r = 1; r < 8; ++r) sum += cs[r][lane];
+    strip_out[lane] = sum;
+}
+
+// Shared-memory barriers of the persistent cell-tile kernel (PTX mbarrier):
+// arrive, and a wait bounded by `limit` SM cycles that gives up at once when
+// the status word already holds an error, latching LBM_E_TIMEOUT otherwise.
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool cbar_test(uint32_t bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ void cbar_wait(uint32_t bar, uint32_t parity, int* status, long long limit)
+{
+    if (cbar_test(bar, parity)) return;
+    const long long t0 = clock64();
+    while (clock64() - t0 < limit && *((volatile int*)status) == 0)
+        if (cbar_test(bar, parity)) return;
+    atomicCAS(status, 0, (int)LBM_E_TIMEOUT);
 }
 
 template <typename IX>
@@ -376,7 +411,9 @@ __global__ void __launch_bounds__(256) k_batch_cells(const __grid_constant__ Cel
     }
     const InstK& I = a.inst[lo];
     __shared__ float cs[8][32];
-    cell_tile<IX>(I, t - I.tile0, *a.kdev + 1 + a.koff, a.buf, a.ncat, a.strip + (long long)(a.tile_base + t) * 32, cs);
+    cs[threadIdx.x >> 5][threadIdx.x & 31] = cell_tile<IX>(I, t - I.tile0, *a.kdev + 1 + a.koff, a.buf, a.ncat);
+    __syncthreads();
+    if (threadIdx.x < 32) tile_column_sum(cs, a.strip + (long long)(a.tile_base + t) * 32);
 }
 
 // Eq. 47 moments of step k for PER_STEP mode, two deterministic passes.
@@ -468,6 +505,11 @@ __global__ void __launch_bounds__(256) k_batch_inst_moments(const BatchArgs a, c
 // column-moment pass of step k - 1 and the per-instance sums of step k - 2
 // (column sums and block partials alternate between two buffers by step
 // parity); after the last step, one more barrier separates the last two passes.
+// Within a block the tiles' column sums pass through two shared row buffers
+// guarded by mbarriers instead of block-wide barriers: every thread arrives on
+// the buffer's "full" barrier, warp 0 alone waits there, adds the rows and
+// arrives on its "empty" barrier, which the warps wait on before they reuse the
+// buffer two tiles later; so warps 1-7 may run up to two tiles ahead of warp 0.
 // The instance constants travel by value in the kernel parameters, as for
 // k_batch_cells (so at most CELL_INST instances), and every read of them is
 // uniform over a block.
@@ -488,6 +530,17 @@ __global__ void __launch_bounds__(256, 4) k_batch_persistent_cells(const __grid_
 {
     const BatchArgs& a = p.b;
     __shared__ float cs[2][8][32];
+    __shared__ __align__(8) unsigned long long cbar[4];   // full[0], full[1], empty[0], empty[1]
+    const uint32_t full0 = smem_u32(&cbar[0]), empty0 = smem_u32(&cbar[2]);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * b), "r"(256) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(empty0 + 8 * b), "r"(32) : "memory");
+        }
+    }
+    __syncthreads();
+    const int wy = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned j = 0;   // tiles of this block so far (all steps): buffer j & 1, its use j >> 1
     const long long t0 = *a.kdev;
     const int gw = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nw = (int)(((long long)gridDim.x * blockDim.x) >> 5);
@@ -502,12 +555,20 @@ __global__ void __launch_bounds__(256, 4) k_batch_persistent_cells(const __grid_
             for (int i = gw; i < a.ninst; i += nw) inst_moments(a, k - 2, i, p.cpart[s & 1]);
         // cell tiles blockIdx.x, blockIdx.x + gridDim.x, ...: equal tiles, so the
         // static split is even to one tile, and no block waits on a counter; the
-        // column-sum rows alternate by tile (one block-wide barrier per tile)
+        // column-sum rows alternate by tile
         float* strip = p.strip[s & 1];
-        int j = 0;
         for (int t = blockIdx.x; t < p.nctiles; t += gridDim.x, ++j) {
             const InstK& I = p.inst[p.tile_inst[t]];
-            cell_tile<IX>(I, t - I.tile0, k, a.buf, a.ncat, strip + (long long)t * 32, cs[j & 1]);
+            const float part = cell_tile<IX>(I, t - I.tile0, k, a.buf, a.ncat);
+            const unsigned b = j & 1u, use = j >> 1;
+            if (use >= 1) cbar_wait(empty0 + 8 * b, (use - 1) & 1u, a.status, a.spin_limit);
+            cs[b][wy][lane] = part;
+            cbar_arrive(full0 + 8 * b);
+            if (wy == 0) {
+                cbar_wait(full0 + 8 * b, use & 1u, a.status, a.spin_limit);
+                tile_column_sum(cs[b], strip + (long long)t * 32);
+                cbar_arrive(empty0 + 8 * b);
+            }
         }
         if (!grid_barrier(a)) return;
     }
