@@ -558,16 +558,16 @@ lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec)
     if (vec == 9) {
         if ((block != 256 && block != 128) || !h->neq || h->q != 15 || h->d.nx % 64 != 0 ||
             h->d.ny % (block / 32) != 0 || 18LL * h->ncell >= (1LL << 31))
-            return fail(h, LBM_E_ARG, "vec 9 (D3Q15 z-walk 16-bit kernel) needs block 256 or 128, nx % 64 == 0 "
-                                      "and ny a multiple of block / 32");
+            return fail(h, LBM_E_ARG, "vec 9 (D3Q15 z-walk 16-bit kernel) needs block 256 or 128, nx % 64 == 0, "
+                                      "ny a multiple of block / 32 and 18 ncell < 2^31");
         h->cfg.block = block;
         h->cfg.vec = vec;
         return LBM_OK;
     }
     if (vec == 7 || vec == 8) {
         if (block != 128 || !tma)
-            return fail(h, LBM_E_ARG, "vec 7 / 8 (TMA-staged D2Q9 16-bit kernel) needs block 128 and "
-                                      "nx % 256 == 0");
+            return fail(h, LBM_E_ARG, "vec 7 / 8 (TMA-staged D2Q9 16-bit kernel) needs block 128, "
+                                      "nx % 256 == 0 and 12 ncell < 2^31");
         h->cfg.block = block;
         h->cfg.vec = vec;
         return LBM_OK;
@@ -576,7 +576,8 @@ lbm_status lbm_cde_set_launch(lbm_cde_t h, int32_t block, int32_t vec)
         (vec == 5 && !pair_ok) || (vec == 6 && !quad))
         return fail(h, LBM_E_ARG, "block must be a multiple of 32 in [32, 256]; vec 1 or 2 (one or two nodes "
                                   "per thread), 5 (node-pair kernel, nx even, 16-bit storage) or 6 (D2Q9 "
-                                  "node-quad kernel, nx % 4 == 0)");
+                                  "node-quad kernel, nx % 4 == 0); vec 5 and 6 use 32-bit offsets: "
+                                  "(q + 3) ncell < 2^31");
     h->cfg.block = block;
     h->cfg.vec = vec;
     return LBM_OK;

@@ -224,3 +224,90 @@ def test_taylor_aris_batch_64_windows(O, mode, tile):
                          u=u.reshape(2, -1)).reshape(c.ny, n)
             cs = slice(half - keep, half + keep + 1)
             assert rel_l2(got[i][:, ix][:, cs], want[:, cs]) <= 1e-5, (i, x0)
+
+
+def _separable(n, seed, lo, hi):
+    """A float32 profile of length n (seeded, smooth)."""
+    g = np.random.default_rng(seed)
+    k = np.arange(n, dtype=np.float64)
+    v = lo + (hi - lo) * 0.5 * (1.0 + np.sin(2.0 * np.pi * k / n * g.integers(1, 5) + g.uniform(0, 6.28)))
+    return v.astype(np.float32)
+
+
+WIDE = [(9, "f32", (256, 1)), (9, "f32", (128, 2)), (9, "bf16", (256, 1)), (9, "f16", (128, 2)),
+        (15, "f32", (64, 2)), (15, "bf16", (128, 1))]
+
+
+@pytest.mark.parametrize("lattice,storage,launch", WIDE, ids=[f"q{q}-{s}-{_launch_id(l)}" for q, s, l in WIDE])
+def test_64bit_offsets_windows(O, lattice, storage, launch):
+    """Grids past 2^31 / (q + 3) nodes (D2Q9 16384 x 11008, D3Q15 512 x 512 x 456)
+    run the step kernels with 64-bit offsets; the launch shapes with 32-bit
+    offsets are refused there. The fields are built on the device from float32
+    profiles by broadcasts (velocity) and products (phi0), float32 operations
+    the host repeats bit for bit, so that oracle windows get the same inputs."""
+    from paper_1404_2363_gb300 import _native as N
+
+    dims = (16384, 11008, 1) if lattice == 9 else (512, 512, 456)
+    nx, ny, nz = dims
+    dim = 2 if lattice == 9 else 3
+    ncell = nx * ny * nz
+    assert (lattice + 3) * ncell >= 2 ** 31
+    nsteps, half = (10, 24) if lattice == 9 else (5, 12)
+    prof = [_separable(n, 40 + i, -0.04, 0.04) for i, n in enumerate((ny, nx, nz))]   # a_x(y), a_y(x), a_z(.)
+    pphi = [_separable(n, 50 + i, 0.6, 1.4) for i, n in enumerate((nx, ny, nz))]
+    sched = W.vortex_schedule(64).astype(np.float32)
+    if dim == 3:
+        sched = np.concatenate([sched, sched[:, :1]], axis=1)
+    dev = torch.device("cuda")
+    px, py, pz = (torch.from_numpy(v).to(dev) for v in pphi)
+    shape = (ny, nx) if dim == 2 else (nz, ny, nx)
+    s = Solver(lattice=lattice, nx=nx, ny=ny, nz=nz, storage=storage)
+    with pytest.raises(N.LbmError):
+        s.set_launch(128, 5 if storage != "f32" else 6)
+    s.set_launch(*launch)
+    D = W.D_eq44_full(1.0) if dim == 2 else np.diag([0.03, 0.02, 0.04])
+    s.set_D(D)
+    u = torch.empty((dim,) + shape, device=dev, dtype=torch.float32)
+    if dim == 2:
+        u[0] = torch.from_numpy(prof[0]).to(dev)[:, None]      # a_x depends on y
+        u[1] = torch.from_numpy(prof[1]).to(dev)[None, :]      # a_y depends on x
+        phi0 = py[:, None] * px[None, :]
+    else:
+        u[0] = torch.from_numpy(prof[0]).to(dev)[None, :, None]
+        u[1] = torch.from_numpy(prof[1]).to(dev)[None, None, :]
+        u[2] = torch.from_numpy(prof[2][:nz]).to(dev)[:, None, None]
+        phi0 = (pz[:, None, None] * py[None, :, None]) * px[None, None, :]
+    s.set_velocity(u, torch.from_numpy(sched).to(dev))
+    s.set_phi(phi0)
+    del u, phi0
+    s.step(nsteps)
+    got = s.get_phi()
+    keep = half - nsteps - 1
+    n = 2 * half + 1
+    c = slice(half - keep, half + keep + 1)
+    sc = sched.astype(np.float64)
+    pts = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (nx // 2 + 3, ny // 3, nz // 2)]
+    for x0, y0, z0 in pts:
+        ix = np.arange(x0 - half, x0 + half + 1) % nx
+        iy = np.arange(y0 - half, y0 + half + 1) % ny
+        if dim == 2:
+            w_phi = np.multiply.outer(pphi[1][iy], pphi[0][ix]).astype(np.float64)
+            wa = np.stack([np.broadcast_to(prof[0][iy][:, None], (n, n)),
+                           np.broadcast_to(prof[1][ix][None, :], (n, n))]).astype(np.float64).reshape(2, -1)
+            p = O.Params(nx=n, ny=n, A=O.A_from_D(D))
+            sub = got[torch.from_numpy(iy).to(dev)][:, torch.from_numpy(ix).to(dev)]
+        else:
+            iz = np.arange(z0 - half, z0 + half + 1) % nz
+            w_phi = np.multiply.outer(np.multiply.outer(pphi[2][iz], pphi[1][iy]), pphi[0][ix]).astype(np.float64)
+            wa = np.stack([np.broadcast_to(prof[0][iy][None, :, None], (n, n, n)),
+                           np.broadcast_to(prof[1][ix][None, None, :], (n, n, n)),
+                           np.broadcast_to(prof[2][iz][:, None, None], (n, n, n))]).astype(np.float64).reshape(3, -1)
+            p = O.default_params_3d(nx=n, ny=n, nz=n, A=O.A_from_D(D, q=15, alpha1=-1.2, alpha2=192.0))
+            t_iz, t_iy, t_ix = (torch.from_numpy(v).to(dev) for v in (iz, iy, ix))
+            sub = got[t_iz][:, t_iy][:, :, t_ix]
+        want = O.run(p, w_phi.reshape(-1), nsteps,
+                     u_of_t=lambda t: wa * sc[t % len(sc)][:, None]).reshape(w_phi.shape)
+        g = sub.cpu().numpy().astype(np.float64)
+        win = (c, c) if dim == 2 else (c, c, c)
+        assert_parity(g[win], want[win], 1e-5 if storage == "f32" else 2e-3, (x0, y0, z0))
+    s.close()
