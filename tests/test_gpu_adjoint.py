@@ -377,3 +377,64 @@ def test_single_step_api_matches_backward():
     da = da.cpu().numpy().astype(np.float64) + init
     ref = da_ref.cpu().numpy().astype(np.float64).reshape(2, -1)
     assert rel_l2(da, ref) < 1e-5
+
+
+@pytest.mark.parametrize("n_grid", [2048, 14000])
+def test_adjoint_64bit_offsets_window(O, n_grid):
+    """Past 2^31 / (q + dim) nodes the reverse-time kernel runs with 64-bit
+    offsets (D2Q9 14000 x 14000). With dL/dphi_N nonzero on a small patch only,
+    every gradient comes from the nodes within nsteps of it, so a periodic
+    oracle box around the patch gives the same dL/dphi0 and dL/da on the box and
+    the same dL/dD. The patch straddles the periodic corner. Inputs are float32
+    profiles broadcast (velocity) or multiplied (phi0) on the device, operations
+    the host repeats bit for bit. (2048^2: the same with 32-bit offsets.)"""
+    from paper_1404_2363_gb300 import workloads as W
+
+    nx = ny = n_grid
+    assert (11 * nx * ny >= 2 ** 31) == (n_grid > 2048)
+    nsteps, ph, H = 6, 4, 4 + 6 + 6
+    dev = torch.device("cuda")
+    # periods of tens of nodes whatever the grid (not periodic across the seam):
+    # the non-equilibrium moments stay well above the FP32 rounding of f
+    k = np.arange(nx, dtype=np.float64)
+    ax = (0.04 * np.sin(2 * np.pi * k / 60 + 0.4)).astype(np.float32)    # a_x(y)
+    ay = (0.03 * np.cos(2 * np.pi * k / 70 + 1.1)).astype(np.float32)    # a_y(x)
+    px = (1.0 + 0.3 * np.sin(2 * np.pi * k / 50)).astype(np.float32)
+    py = (1.0 + 0.2 * np.cos(2 * np.pi * k / 40 + 0.3)).astype(np.float32)
+    sched = W.vortex_schedule(64).astype(np.float32)
+    D = W.D_ANISO
+    u = torch.empty((2, ny, nx), device=dev, dtype=torch.float32)
+    u[0] = torch.from_numpy(ax).to(dev)[:, None]
+    u[1] = torch.from_numpy(ay).to(dev)[None, :]
+    phi0 = torch.from_numpy(py).to(dev)[:, None] * torch.from_numpy(px).to(dev)[None, :]
+    x0, y0 = 1, ny - 2                                   # patch centre next to the corner
+    ix = np.arange(x0 - H, x0 + H + 1) % nx
+    iy = np.arange(y0 - H, y0 + H + 1) % ny
+    gw = np.zeros((2 * H + 1, 2 * H + 1), dtype=np.float32)
+    gw[H - ph:H + ph + 1, H - ph:H + ph + 1] = np.random.default_rng(17).standard_normal((2 * ph + 1, 2 * ph + 1))
+    g = torch.zeros((ny, nx), device=dev, dtype=torch.float32)
+    t_iy, t_ix = torch.from_numpy(iy).to(dev), torch.from_numpy(ix).to(dev)
+    g[t_iy[:, None], t_ix[None, :]] = torch.from_numpy(gw).to(dev)
+
+    s = Solver(nx=nx, ny=ny)
+    s.set_D(D)
+    s.set_velocity(u, torch.from_numpy(sched).to(dev))
+    s.forward_ckpt(phi0, nsteps)
+    dphi0, dD, _, da = s.backward(g, want_da=True)
+    got_p = dphi0[t_iy[:, None], t_ix[None, :]].cpu().numpy().astype(np.float64)
+    got_a = da[:, t_iy[:, None], t_ix[None, :]].cpu().numpy().astype(np.float64)
+    s.close()
+
+    n = 2 * H + 1
+    wphi = np.multiply.outer(py[iy], px[ix]).astype(np.float64).reshape(-1)
+    wa = np.stack([np.broadcast_to(ax[iy][:, None], (n, n)), np.broadcast_to(ay[ix][None, :], (n, n))])
+    wa = wa.astype(np.float64).reshape(2, -1)
+    sc = sched.astype(np.float64)
+    p = O.Params(nx=n, ny=n, A=O.A_from_D(D))
+    gp, gD, du, _ = O.adjoint_gradients(p, wphi, nsteps, gw.astype(np.float64).reshape(-1),
+                                        u_of_t=lambda t: wa * sc[t % len(sc)][:, None])
+    st = sc[np.arange(nsteps) % len(sc)]
+    want_a = np.einsum("td,tdc->dc", st, du).reshape(2, n, n)
+    assert rel_l2(got_p, gp.reshape(n, n)) < 1e-5
+    assert rel_l2(got_a, want_a) < 1e-4
+    assert np.abs(dD - gD).max() <= 1e-4 * np.abs(gD).max()
