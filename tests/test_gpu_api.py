@@ -90,3 +90,39 @@ def test_rates_follow_eq36():
     A, rates = s.rates()
     assert np.allclose(A, O.A_from_D(D), rtol=1e-12)
     assert abs(rates[4] - A[0, 0]) < 1e-6 and abs(rates[6] - A[1, 1]) < 1e-6
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_zero_steps_are_a_no_op_and_negative_counts_rejected(storage):
+    case = Case(storage=storage, steps=7)
+    phi0, a, sched = case.inputs()
+    got, s = run_gpu(case, phi0, a, sched)
+    s.step(0)
+    assert np.array_equal(s.get_phi().cpu().numpy(), got)
+    with pytest.raises(N.LbmError) as e:
+        s.step(-1)
+    assert e.value.status == N.LBM_E_ARG
+    s.step(1)                      # the handle is still usable
+    assert np.isfinite(s.get_phi().cpu().numpy()).all()
+    s.close()
+
+
+def test_batch_zero_steps_are_a_no_op_and_negative_counts_rejected():
+    from paper_1404_2363_gb300.batch import Batch, poiseuille_row
+
+    u = poiseuille_row(9, 0.05)
+    ch = {"nx": 64, "ny": 9, "bc": ("noflux", "noflux"), "D": [[0.02, 0.0], [0.0, 0.02]], "u_row": u,
+          "x_ref0": 20.0, "x_ref_velocity": 0.0}
+    phi = np.random.default_rng(2).uniform(0.5, 1.5, (9, 64)).astype(np.float32)
+    b = Batch([ch, dict(ch, nx=96)], graph_steps=4)
+    b.set_phi([phi, np.tile(phi, (1, 2))[:, :96]])
+    b.run(3)
+    before = [g.cpu().numpy() for g in b.get_phi()]
+    m = b.run(0)
+    assert m.shape == (0, 2, 3)
+    assert all(np.array_equal(x, g.cpu().numpy()) for x, g in zip(before, b.get_phi()))
+    with pytest.raises(N.LbmError) as e:
+        b.run(-1, moments=False)
+    assert e.value.status == N.LBM_E_ARG
+    assert np.isfinite(b.run(2)).all()
+    b.close()
