@@ -78,9 +78,13 @@ int adjoint_rows(long long nx, long long ny, long long nz, int sms)
 // pulls of one node only, so every thread writes its own addresses: (j, x - e_j)
 // for the sources in range, and (k, x) for the populations that leave through
 // a wall (zero unless a bounce-back pull read them).
-template <class L, int UK, int WM, bool DA, typename IX>
+// QUAD: the u^2 terms of the MRT-B1/B2 equilibria (D2Q9 with a velocity only);
+// a compile-time choice, as a run-time test left their arithmetic predicated
+// in every node of the other models (7 % more instructions).
+template <class L, int UK, int WM, bool DA, typename IX, bool QUAD>
 __global__ void __launch_bounds__(256, (L::Q == 9 && !DA && WM < 2) ? 4 : 3) k_adjoint(const AdjArgs a)
 {
+    static_assert(!QUAD || (L::Q == 9 && UK != U_NONE), "u^2 terms only for D2Q9 with a velocity");
     constexpr bool WALLS = WM == 1, BOX = WM == 2;
     constexpr int Q = L::Q, DIM = L::DIM, NG = ngrad<L>();
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -241,9 +245,8 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA && WM < 2) ? 4 : 3) k_a
             v[3 + 2 * d] = u[d];
             v[4 + 2 * d] = -u[d];
         }
-        // MRT-B1/B2 (D2Q9, Eq. 38-39): the u^2 terms of m^eq (c.b1 = c.g7 = 0 otherwise)
-        const bool quad = L::Q == 9 && (c.b1 != 0.f || c.g7 != 0.f);
-        if (quad) {
+        // MRT-B1/B2 (D2Q9, Eq. 38-39): the u^2 terms of m^eq
+        if constexpr (QUAD) {
             const float u2 = fmaf(ux, ux, uy * uy);
             v[1] = fmaf(c.b1, u2, c.meq1);
             v[2] = fmaf(c.b2, u2, c.meq2);
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(256, (L::Q == 9 && !DA && WM < 2) ? 4 : 3) k_a
             float gu[DIM];   // dL/du(k) / phi = b . dv/du
 #pragma unroll
             for (int d = 0; d < DIM; ++d) gu[d] = b[3 + 2 * d] - b[4 + 2 * d];
-            if (quad) {
+            if constexpr (QUAD) {
                 const float q12 = fmaf(c.b1, b[1], c.b2 * b[2]);
                 gu[0] += fmaf(2.f * ux, fmaf(c.g7, b[7], q12), c.g8 * uy * b[8]);
                 gu[1] += fmaf(2.f * uy, fmaf(-c.g7, b[7], q12), c.g8 * ux * b[8]);
@@ -524,17 +527,21 @@ template <class L, int UK, typename IX, int WM>
 static cudaError_t adj_wm(const AdjArgs& a, cudaStream_t st, bool reduce)
 {
     dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)((a.ny + a.rows - 1) / a.rows), (unsigned)a.nz);
+    // the u^2 terms of MRT-B1/B2 (zero coefficients for the other models; with no
+    // velocity they vanish)
+    constexpr bool QOK = L::Q == 9 && UK != U_NONE;
+    const bool quad = QOK && (a.c.b1 != 0.f || a.c.g7 != 0.f);
     if constexpr (UK == U_FIELD) {
         if (a.du_acc != nullptr) {
-            k_adjoint<L, UK, WM, true, IX><<<grid, 256, 0, st>>>(a);
+            if (quad) k_adjoint<L, UK, WM, true, IX, QOK><<<grid, 256, 0, st>>>(a);
+            else k_adjoint<L, UK, WM, true, IX, false><<<grid, 256, 0, st>>>(a);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess || !reduce) return e;
             return grad_reduce<L>(a, a.partials, 1, 0, st);
         }
     }
-    {
-        k_adjoint<L, UK, WM, false, IX><<<grid, 256, 0, st>>>(a);
-    }
+    if (quad) k_adjoint<L, UK, WM, false, IX, QOK><<<grid, 256, 0, st>>>(a);
+    else k_adjoint<L, UK, WM, false, IX, false><<<grid, 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !reduce) return e;
     return grad_reduce<L>(a, a.partials, 1, 0, st);
