@@ -79,8 +79,8 @@ int adjoint_rows(long long nx, long long ny, long long nz, int sms)
 // for the sources in range, and (k, x) for the populations that leave through
 // a wall (zero unless a bounce-back pull read them).
 // QUAD: the u^2 terms of the MRT-B1/B2 equilibria (D2Q9 with a velocity only);
-// a compile-time choice, as a run-time test left their arithmetic predicated
-// in every node of the other models (7 % more instructions).
+// a compile-time choice: behind a run-time test the kernel executed 7 % more
+// instructions for the other models, which never take them.
 template <class L, int UK, int WM, bool DA, typename IX, bool QUAD>
 __global__ void __launch_bounds__(256, (L::Q == 9 && !DA && WM < 2) ? 4 : 3) k_adjoint(const AdjArgs a)
 {
