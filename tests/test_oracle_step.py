@@ -106,6 +106,10 @@ def test_covariance_growth_without_deviation_mrt_a(O):
     for model in (O.MRT_B1, O.MRT_B2):
         gb = _growth(O, O.Params(nx=n, ny=n, A=A, model=model), u, n, 200, 260, x0=x0)[1]
         assert np.abs(gb - 2 * D).max() < 1e-10
+    # the growth above is 2 D with A = (3 D + I/2)^-1, i.e. k = 1/3, for the B models
+    # whatever constants their equilibria carry (MRT-B1's u = 0 part is alpha2 = 4)
+    for model, a2 in ((O.MRT_B1, 4.0), (O.MRT_B2, 8.0), (O.MRT_B3, 8.0)):
+        assert O.diffusion_factor(9, -8.0, a2, model) == 1.0 / 3.0
 
 
 def test_noflux_wall_rule_sec32(O):
