@@ -364,12 +364,14 @@ typedef struct {
                                 the next step's cells, and join the batch's stream at the end
                                 of each run) */
     int32_t tile_rows;       /* PERSISTENT work tiles: 0 (default) the 32 x 16 cell tiles of
-                                PER_STEP taken by whole blocks, with the moment passes between
-                                grid barriers inside the launch; 1 .. 1024: tiles of 32 columns
-                                x tile_rows rows, one warp each, one node per thread */
+                                PER_STEP taken by whole blocks, one grid barrier per step, the
+                                moment passes of steps k - 1 and k - 2 run ahead of the cells of
+                                step k inside the launch; 1 .. 1024: tiles of 32 columns x
+                                tile_rows rows, one warp each, one node per thread */
     int32_t graph_steps;     /* steps per captured CUDA graph (ring of moments), 1 .. 4096 */
-    int64_t barrier_timeout_cycles; /* clock64 cycles a CTA waits at a grid barrier before the
-                                launch gives up with LBM_E_TIMEOUT (default 2e9, about 1 s) */
+    int64_t barrier_timeout_cycles; /* clock64 cycles a CTA waits at a grid barrier (and, on
+                                cell tiles, at its shared-memory barriers) before the launch
+                                gives up with LBM_E_TIMEOUT (default 2e9, about 1 s) */
     void* (*alloc)(size_t bytes, void* ctx);
     void (*free_)(void* ptr, void* ctx);
     void* alloc_ctx;
